@@ -1,0 +1,247 @@
+"""FP64 oracle of the split pressure-gradient projection, Sec. 5.4 of
+Poblador-Ibanez & Sirignano (arXiv 2103.01874).
+
+TEST INFRASTRUCTURE: only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg may use this module.  It shares no code with the CUDA path.
+
+The method reaches its result exactly (a direct, non-iterative solve of the
+constant-coefficient Poisson equation, Sec. 5.4 text after Eq. (34)), so this
+module is the plain definition of that discrete result, written with numpy and
+scipy library transforms as steps:
+
+  p_hat  = 2 p^n - p^{n-1}                                  Eq. (32)
+  rho_0  = min(rho)                                          Eq. (32) text
+  f      = D[(1 - rho_0/rho_f) G p_hat] + (rho_0/dt)(D u* - S)   Eq. (34)
+  L p    = f,  L = D G,  mean(p) = 0                         Eq. (34)
+  u^{n+1} = u* - dt [G p / rho_0 + (1/rho_f - 1/rho_0) G p_hat]   Eq. (33)
+
+Discretisation ("standard finite-volume techniques" on the uniform staggered
+mesh, Sec. 5 and the paragraph after Eq. (34)):
+  G  cell -> face difference; zero on the two wall planes of y (Neumann);
+  D  face -> cell divergence;  L = D G is the 7-point Laplacian;
+  rho_f the face density, arithmetic mean of the two cells (default) or
+        harmonic mean (option) -- the paper leaves the face rule for rho open.
+Periodic in x and z, walls (homogeneous Neumann for p) in y.
+
+The solve diagonalises L exactly: DFT in x and z (numpy.fft), DCT-II in y
+(scipy.fft, orthonormal), divide by the eigenvalues
+  lam = -(4/dx^2) sin^2(pi kx/Nx) - (4/dy^2) sin^2(pi ky/(2 Ny)) - (4/dz^2) sin^2(pi kz/Nz)
+and drop the zero mode, which makes p the zero-mean least-squares solution.
+
+Pins (tests/test_oracle_pins.py): discrete eigenfunctions, a brute-force
+7-point stencil, dense LU of L on small grids, the divergence identity
+D u^{n+1} = S, the constant-density limit, split exactness when
+p^n = p^{n-1} solves Eq. (30), zero mean, and shift/reflection symmetry.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.fft as sfft
+
+FACE_ARITHMETIC = 0
+FACE_HARMONIC = 1
+
+
+def spacings(shape, lengths):
+    nz, ny, nx = shape
+    lx, ly, lz = lengths
+    return lx / nx, ly / ny, lz / nz
+
+
+# ----------------------------------------------------------------------------
+# Discrete operators on the staggered mesh (Sec. 5, uniform MAC grid)
+# ----------------------------------------------------------------------------
+
+def grad(q, h):
+    """G: cell field [Nz][Ny][Nx] -> face fields (gx [Nz][Ny][Nx],
+    gy [Nz][Ny+1][Nx], gz [Nz][Ny][Nx]).  gx[..., i] = (q_i - q_{i-1})/dx with
+    periodic wrap; gy on the walls j = 0, Ny is zero (homogeneous Neumann)."""
+    dx, dy, dz = h
+    nz, ny, nx = q.shape
+    gx = (q - np.roll(q, 1, axis=2)) / dx
+    gz = (q - np.roll(q, 1, axis=0)) / dz
+    gy = np.zeros((nz, ny + 1, nx))
+    gy[:, 1:ny, :] = (q[:, 1:, :] - q[:, :-1, :]) / dy
+    return gx, gy, gz
+
+
+def div(a, b, c, h):
+    """D: face fields -> cell field.  (a_{i+1} - a_i)/dx + (b_{j+1} - b_j)/dy
+    + (c_{k+1} - c_k)/dz, periodic in i and k."""
+    dx, dy, dz = h
+    return ((np.roll(a, -1, axis=2) - a) / dx
+            + (b[:, 1:, :] - b[:, :-1, :]) / dy
+            + (np.roll(c, -1, axis=0) - c) / dz)
+
+
+def laplacian(q, h):
+    """L = D G, the 7-point operator of Eq. (34)'s left side."""
+    return div(*grad(q, h), h)
+
+
+def face_density(rho, rule=FACE_ARITHMETIC):
+    """rho on the faces.  Wall faces of y get the adjacent cell's value; they
+    are never used because G = 0 there."""
+    nz, ny, nx = rho.shape
+    left_x = np.roll(rho, 1, axis=2)
+    left_z = np.roll(rho, 1, axis=0)
+    ry = np.empty((nz, ny + 1, nx))
+    ry[:, 0, :] = rho[:, 0, :]
+    ry[:, ny, :] = rho[:, ny - 1, :]
+    lo, hi = rho[:, :-1, :], rho[:, 1:, :]
+    if rule == FACE_ARITHMETIC:
+        rx = 0.5 * (left_x + rho)
+        rz = 0.5 * (left_z + rho)
+        ry[:, 1:ny, :] = 0.5 * (lo + hi)
+    elif rule == FACE_HARMONIC:
+        rx = 2.0 / (1.0 / left_x + 1.0 / rho)
+        rz = 2.0 / (1.0 / left_z + 1.0 / rho)
+        ry[:, 1:ny, :] = 2.0 / (1.0 / lo + 1.0 / hi)
+    else:
+        raise ValueError("face rule")
+    return rx, ry, rz
+
+
+def rho0_of(rho):
+    """rho_0 = min(rho), the text after Eq. (32)."""
+    return float(np.min(rho))
+
+
+# ----------------------------------------------------------------------------
+# Eq. (34): right-hand side
+# ----------------------------------------------------------------------------
+
+def ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC):
+    """f = D[(1 - rho_0/rho_f) G p_hat] + (rho_0/dt)(D u* - S), Eq. (34), with
+    p_hat = 2 p^n - p^{n-1} (Eq. (32))."""
+    h = spacings(rho.shape, lengths)
+    p_hat = 2.0 * p_n - p_nm1
+    gx, gy, gz = grad(p_hat, h)
+    rx, ry, rz = face_density(rho, rule)
+    split = div((1.0 - rho0 / rx) * gx, (1.0 - rho0 / ry) * gy, (1.0 - rho0 / rz) * gz, h)
+    return split + (rho0 / dt) * (div(u, v, w, h) - S)
+
+
+# ----------------------------------------------------------------------------
+# Eq. (34): direct solve of L p = f (the paper's FFT Poisson solver)
+# ----------------------------------------------------------------------------
+
+def eigenvalues(shape, lengths):
+    """Eigenvalues of L for the Fourier (x, z) x cosine (y) modes, shape
+    [Nz][Ny][Nx//2+1] matching rfft in x, full fft in z, DCT-II in y."""
+    nz, ny, nx = shape
+    dx, dy, dz = spacings(shape, lengths)
+    kx = np.arange(nx // 2 + 1)
+    ky = np.arange(ny)
+    kz = np.arange(nz)
+    lx = -(4.0 / dx**2) * np.sin(math.pi * kx / nx) ** 2
+    ly = -(4.0 / dy**2) * np.sin(math.pi * ky / (2 * ny)) ** 2
+    lz = -(4.0 / dz**2) * np.sin(math.pi * kz / nz) ** 2
+    return lz[:, None, None] + ly[None, :, None] + lx[None, None, :]
+
+
+def ppe_solve(f, lengths):
+    """Zero-mean p with L p = f - mean(f) (the zero mode is dropped)."""
+    nz, ny, nx = f.shape
+    fh = np.fft.rfft(f, axis=2)
+    fh = np.fft.fft(fh, axis=0)
+    fh = sfft.dct(fh, type=2, axis=1, norm="ortho")
+    lam = eigenvalues(f.shape, lengths)
+    lam[0, 0, 0] = 1.0
+    ph = fh / lam
+    ph[0, 0, 0] = 0.0
+    ph = sfft.idct(ph, type=2, axis=1, norm="ortho")
+    ph = np.fft.ifft(ph, axis=0)
+    return np.fft.irfft(ph, n=nx, axis=2)
+
+
+def residual(f, p, lengths):
+    h = spacings(f.shape, lengths)
+    return f - laplacian(p, h)
+
+
+# ----------------------------------------------------------------------------
+# Eq. (33): velocity correction
+# ----------------------------------------------------------------------------
+
+def ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC):
+    """u^{n+1} = u* - dt [G p / rho_0 + (1/rho_f - 1/rho_0) G p_hat] on every
+    face, Eq. (33).  On the wall faces G = 0, so v is returned unchanged."""
+    h = spacings(rho.shape, lengths)
+    p_hat = 2.0 * p_n - p_nm1
+    gpx, gpy, gpz = grad(p, h)
+    ghx, ghy, ghz = grad(p_hat, h)
+    rx, ry, rz = face_density(rho, rule)
+    u1 = u - dt * (gpx / rho0 + (1.0 / rx - 1.0 / rho0) * ghx)
+    v1 = v - dt * (gpy / rho0 + (1.0 / ry - 1.0 / rho0) * ghy)
+    w1 = w - dt * (gpz / rho0 + (1.0 / rz - 1.0 / rho0) * ghz)
+    return u1, v1, w1
+
+
+def ppe_project(u, v, w, S, rho, p_n, p_nm1, dt, lengths, rho0=None, rule=FACE_ARITHMETIC):
+    """The whole projection step: returns dict(f, p, u, v, w, rho0)."""
+    if rho0 is None or rho0 <= 0.0:
+        rho0 = rho0_of(rho)
+    f = ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule)
+    p = ppe_solve(f, lengths)
+    u1, v1, w1 = ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule)
+    return dict(f=f, p=p, u=u1, v=v1, w=w1, rho0=rho0)
+
+
+def project_fields(fl, rule=FACE_ARITHMETIC, rho0=None):
+    """ppe_project on a paper_2103_01874_gb300.fields.Fields-like object."""
+    return ppe_project(fl.u, fl.v, fl.w, fl.S, fl.rho, fl.p_n, fl.p_nm1, fl.dt,
+                       (fl.lx, fl.ly, fl.lz), rho0=rho0, rule=rule)
+
+
+# ----------------------------------------------------------------------------
+# Eq. (30): the unsplit variable-coefficient equation (exactness reference)
+# ----------------------------------------------------------------------------
+
+def var_coeff_apply(q, rho, lengths, rule=FACE_ARITHMETIC):
+    """A q = D[(1/rho_f) G q], the left side of Eq. (30)."""
+    h = spacings(rho.shape, lengths)
+    gx, gy, gz = grad(q, h)
+    rx, ry, rz = face_density(rho, rule)
+    return div(gx / rx, gy / ry, gz / rz, h)
+
+
+def dense_operator(apply, shape):
+    """Columns of a linear cell-field operator, by applying it to unit cells."""
+    n = int(np.prod(shape))
+    mat = np.empty((n, n))
+    e = np.zeros(n)
+    for c in range(n):
+        e[c] = 1.0
+        mat[:, c] = apply(e.reshape(shape)).ravel()
+        e[c] = 0.0
+    return mat
+
+
+def dense_zero_mean_solve(mat, rhs):
+    """Solve mat x = rhs - mean(rhs) with sum(x) = 0 by dense LU of the system
+    bordered with the constant vector (mat has the constants as null space)."""
+    n = mat.shape[0]
+    big = np.zeros((n + 1, n + 1))
+    big[:n, :n] = mat
+    big[:n, n] = 1.0
+    big[n, :n] = 1.0
+    b = np.zeros(n + 1)
+    b[:n] = rhs.ravel() - rhs.mean()
+    return np.linalg.solve(big, b)[:n].reshape(rhs.shape)
+
+
+def var_coeff_solve_dense(rhs, rho, lengths, rule=FACE_ARITHMETIC):
+    """Zero-mean q with D[(1/rho_f) G q] = rhs (Eq. (30)) by dense LU: small grids."""
+    mat = dense_operator(lambda q: var_coeff_apply(q, rho, lengths, rule), rho.shape)
+    return dense_zero_mean_solve(mat, rhs)
+
+
+def rel_linf(a, b):
+    """max|a - b| / max|b|."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = float(np.max(np.abs(b)))
+    return float(np.max(np.abs(a - b))) / (den if den > 0 else 1.0)
