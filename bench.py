@@ -1,0 +1,403 @@
+"""Throughput of the split pressure-gradient projection on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: the 256^3 multimode two-phase problem (density 640/60, 6-cell tanh
+layer, 8 seeded interface modes), box 2 pi, periodic x and z, walls in y.  One
+step = one whole projection (rho_0, Eq. (34) right-hand side, direct Poisson
+solve, Eq. (33) correction) through the C ABI (ppe_project).  The headline form
+solves in FP32 inside an FP64-residual iterative refinement to a relative
+residual of 1e-10; the plain FP64 form is timed beside it.  Inputs (7 fields,
+~0.94 GB) are larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  For N > 1 every rank runs an independent replica
+of the workload on its own GPU (no collective on the data path); value is the
+total solves of all ranks over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference arm: a plain
+numpy/scipy restatement of the paper's method) on this host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PPE projection solves/s & Gpts/s at 256³ (FP64 vs FP32+refine @1e-10); % HBM roof"
+WORKLOAD = "multimode_256: 256x256x256, density 640/60, FP32 solve + FP64 refinement to rel residual 1e-10"
+NX = NY = NZ = 256
+N_CELLS = NX * NY * NZ
+F_BYTES = 8 * N_CELLS
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA throughput of a GB300 as measured by an FMA-chain probe on this machine
+# (1.19 TFLOP/s; 152 SMs at ~2.0 GHz), used as the ALU roof of FP64-bound kernels.
+FP64_TFLOPS_MEASURED = 1.19
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (unique bytes a launch must move)
+# ---------------------------------------------------------------------------
+def kernel_bytes(kernel: str, fp32: bool) -> float:
+    F = float(F_BYTES)
+    Fv = F * (NY + 1) / NY
+    spec = (NX // 2 + 1) * NY * NZ * (8 if fp32 else 16)
+    table = {
+        "k_xfwd_rhs": 6 * F + Fv + (F if fp32 else 0) + spec,   # 7 inputs; f kept (refine); spectrum
+        "k_xfwd_f": F + spec,
+        "k_xfwd_resid": 2 * F + spec,                           # f, p -> spectrum
+        "k_zfft_fwd": 2 * spec,
+        "k_ythomas": 2 * spec,
+        "k_zfft_inv": 2 * spec,
+        "k_xinv": spec + F,
+        "k_xinv_accum": spec + 2 * F,
+        "k_correct": 6 * F + Fv + F + 2 * F + Fv,               # u*,v*,w*,rho,p^n,p^{n-1},p ; u,v,w
+        "k_rho_min": F,
+    }
+    return table.get(kernel, 0.0)
+
+
+def step_min_bytes(fp32: bool, sweeps: int) -> float:
+    """Minimal-pass traffic of one projection: 21F for FP64 (7 inputs read,
+    two half-spectrum round trips, 6 fields re-read by the correction, 4
+    outputs written); FP32 + refinement (21 + 6k)F for k sweeps."""
+    return F_BYTES * (21 + (6 * sweeps if fp32 else 0))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2103_01874_gb300 import fields, ppe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    fl = fields.multimode_256(seed=2 + rank)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in fl.arrays().items()}
+    c = fl.shape
+    out = dict(p=torch.empty(c, dtype=torch.float64, device=dev), u=torch.empty_like(d["u"]),
+               v=torch.empty_like(d["v"]), w=torch.empty_like(d["w"]))
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(plan, steps, warmup, profile=False):
+        for _ in range(warmup):
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt,
+                         out["p"], out["u"], out["v"], out["w"])
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        plan.profile(profile)
+        if profile:
+            plan.profile_read()  # clear
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt,
+                         out["p"], out["u"], out["v"], out["w"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        kt = plan.profile_read() if profile else {}
+        plan.profile(False)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, kt
+
+    steps, warmup = args.steps, args.warmup
+    plan32 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, refine_tol=1e-10,
+                      max_sweeps=args.max_sweeps, stream=stream)
+    with ClockSampler(dev.index if world > 1 else 0) as clk:
+        ms32, _ = timed(plan32, steps, warmup)
+    clocks = clk.summary()
+    info32 = plan32.info(allow_not_converged=True)
+    # per-kernel event timing over a second timed region of the same steps
+    ms32p, kt32 = timed(plan32, steps, 1, profile=True)
+
+    plan64 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP64, stream=stream)
+    ms64, _ = timed(plan64, max(1, steps // 2), max(3, warmup // 2))
+    steps64 = max(1, steps // 2)
+    ms64p, kt64 = timed(plan64, steps64, 1, profile=True)
+
+    # e2e: the same projection from pinned host buffers through ppe_project_host
+    hin = {k: torch.from_numpy(v).pin_memory() for k, v in fl.arrays().items()}
+    hout = dict(p=torch.empty(c, dtype=torch.float64).pin_memory(),
+                u=torch.empty(c, dtype=torch.float64).pin_memory(),
+                v=torch.empty(fl.v.shape, dtype=torch.float64).pin_memory(),
+                w=torch.empty(c, dtype=torch.float64).pin_memory())
+
+    def host_step():
+        plan32.project_host(hin["u"], hin["v"], hin["w"], hin["S"], hin["rho"], hin["p_n"], hin["p_nm1"], fl.dt,
+                            hout["p"], hout["u"], hout["v"], hout["w"])
+
+    for _ in range(2):
+        host_step()
+    barrier()
+    e_steps = max(2, steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        host_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(v.numel() * 8 for v in hin.values())
+    d2h = sum(v.numel() * 8 for v in hout.values())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    hbm, hbm_src = peaks()
+    per_step32 = ms32 / steps
+    value = world * steps / (ms32 * 1e-3)
+    # dominant kernel of the headline form
+    dom = max(kt32.items(), key=lambda kv: kv[1][1]) if kt32 else (None, (0, 0.0))
+    dname, (dl, dms) = dom
+    avg_ms = dms / dl if dl else float("nan")
+    step_total = sum(v[1] for v in kt32.values()) or 1.0
+    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0], "share": v[1] / step_total,
+                   "GBps": (kernel_bytes(k, True) / (1e-3 * v[1] / v[0]) / 1e9) if kernel_bytes(k, True) else None}
+               for k, v in sorted(kt32.items(), key=lambda kv: -kv[1][1])}
+    k64_total = sum(v[1] for v in kt64.values()) or 1.0
+    kernels64 = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0], "share": v[1] / k64_total,
+                     "GBps": (kernel_bytes(k, False) / (1e-3 * v[1] / v[0]) / 1e9) if kernel_bytes(k, False) else None}
+                 for k, v in sorted(kt64.items(), key=lambda kv: -kv[1][1])}
+    dbytes = kernel_bytes(dname, True) if dname else 0.0
+    achieved = dbytes / (avg_ms * 1e-3) / 1e9 if dbytes and avg_ms > 0 else None
+    roof = {"kernel": dname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src}
+    sweeps = info32.sweeps
+    step_bytes = step_min_bytes(True, sweeps)
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": warmup,
+        "ms_per_step": per_step32,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 solve + f64 residual/rhs/correction",
+        "data": "synthetic (seeded two-phase fields, numpy default_rng)",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "precision": "fp32+fp64-refine",
+                   "refine_tol": 1e-10, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs 0.94 GB > L2 (no flush needed)"},
+        "gpts_per_s": value * N_CELLS / 1e9,
+        "sweeps": sweeps,
+        "rel_residual": info32.rel_residual,
+        "step_roofline": {"min_pass_bytes": step_bytes, "achieved_GBps": step_bytes / (per_step32 * 1e-3) / 1e9,
+                          "frac_of_hbm": step_bytes / (per_step32 * 1e-3) / 1e9 / hbm},
+        "fp64": {"solves_per_s": world * steps64 / (ms64 * 1e-3) if ms64 else None,
+                 "ms_per_step": ms64 / max(1, steps // 2),
+                 "gpts_per_s": world * steps64 / (ms64 * 1e-3) * N_CELLS / 1e9,
+                 "step_min_pass_frac_of_hbm": step_min_bytes(False, 0) / (ms64 / steps64 * 1e-3) / 1e9 / hbm,
+                 "kernels": kernels64},
+        "roofline": roof,
+        "kernels": kernels,
+        "clocks": clocks,
+        "e2e": {"value": world * e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(v[0] for v in kt32.values()) * steps // max(1, steps)),
+        "gpu_launches_note": "kernels per timed region of the headline form (profiled re-run of the same steps)",
+        "profiled_ms_per_step": ms32p / steps,
+    }
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args)
+    if dist is not None:
+        dist.destroy_process_group()
+    return res
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm / cpu_baseline)
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import ppe_oracle as O
+from paper_2103_01874_gb300 import fields
+fl = fields.multimode_256()
+times = []
+for s in range({n}):
+    t = time.perf_counter()
+    O.project_fields(fl)
+    times.append(time.perf_counter() - t)
+print(json.dumps(times))
+"""
+
+
+def oracle_times(n: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=n)], capture_output=True,
+                       text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args):
+    n = max(1, args.cpu_solves)
+    times = oracle_times(n)
+    return {"value": n / sum(times), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} whole 256^3 projections (FP64 numpy/scipy oracle, 1 thread), "
+                      f"{sum(times):.1f} s of CPU work; best {min(times):.2f} s/solve"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return None
+    times = oracle_times(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = len(timed) / total
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded two-phase fields, numpy default_rng)",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "precision": "fp64 (oracle)",
+                   "parallelism": "single host core"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one whole 256^3 projection; {len(timed)} timed steps"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--max-sweeps", type=int, default=8)
+    ap.add_argument("--cpu-solves", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        from paper_2103_01874_gb300 import build
+        build.build()
+        res = run_gpu(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

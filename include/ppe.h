@@ -1,0 +1,181 @@
+/*
+ * ppe.h -- C ABI of libppe: the split pressure-gradient projection step of
+ * Poblador-Ibanez & Sirignano, "A Volume-of-Fluid method for variable-density,
+ * two-phase flows at supercritical pressure" (arXiv 2103.01874), Sec. 5.4,
+ * running on one NVIDIA GB300 (sm_103a).
+ *
+ * The paper states the problem as: given the predicted velocity u* (called u^p
+ * in Eq. (29)), the new density rho^{n+1}, the divergence constraint
+ * S = div u^{n+1} (Eq. (31)), the pressures p^n, p^{n-1} and dt, find p^{n+1}
+ * and u^{n+1}.  With p_hat = 2 p^n - p^{n-1} and rho_0 = min(rho) (Eq. (32)):
+ *
+ *   L p^{n+1} = D[(1 - rho_0/rho_f) G p_hat] + (rho_0/dt)(D u* - S)     Eq. (34)
+ *   u^{n+1}   = u* - dt [G p^{n+1}/rho_0 + (1/rho_f - 1/rho_0) G p_hat]  Eq. (33)
+ *
+ * G is the cell-to-face difference, D the face-to-cell divergence and L = D G
+ * the 7-point Laplacian of the uniform staggered (MAC) mesh (Sec. 5); rho_f is
+ * the face density (arithmetic mean of the two cells by default).  Eq. (34) has
+ * constant coefficients and is solved directly, without iteration, by a fast
+ * Poisson solver (the paragraph after Eq. (34)): real DFT in x, complex DFT in
+ * z (both periodic), and a tridiagonal solve per (kx, kz) wavenumber in y
+ * (homogeneous Neumann walls).  p^{n+1} is returned with zero mean (the zero
+ * mode is dropped, which also removes any mean of the right-hand side).
+ *
+ * Array layout (every field argument): C order with x fastest,
+ *   cell fields (S, rho, p^n, p^{n-1}, p, f) and u, w:  index (k*ny + j)*nx + i,
+ *   v (y faces, walls at j = 0 and j = ny):              index (k*(ny+1) + j)*nx + i.
+ * u[k][j][i] is the x face between cells i-1 and i (periodic), w[k][j][i] the z
+ * face between cells k-1 and k (periodic).  All values are IEEE FP64.
+ *
+ * Ownership: every field pointer is DEVICE memory owned by the caller, unless
+ * the function name ends in _host.  The plan owns its workspace (spectrum,
+ * twiddle and tridiagonal tables, reduction scalars) and frees it in
+ * ppe_destroy.  Calls are asynchronous on the plan's stream; errors found on
+ * the host are returned at once, device-side results (sweeps, residual, rho_0)
+ * are read with ppe_get_info, which synchronises the stream.
+ *
+ * Aliasing: inputs may not alias outputs, except u_out == u, v_out == v,
+ * w_out == w (in-place correction) in ppe_correct and ppe_project.
+ *
+ * Error behaviour: a NULL plan or pointer, dt <= 0, or lengths <= 0 give
+ * PPE_ERR_INVALID_ARG; a dimension that is not 2^a 3^b, below 8, above 1024,
+ * or an odd nx, gives PPE_ERR_UNSUPPORTED_SIZE; allocation failure gives
+ * PPE_ERR_OUT_OF_MEMORY; a CUDA launch error gives PPE_ERR_CUDA.  No call
+ * falls back to the host: without a usable GPU every compute call fails.
+ */
+#ifndef PPE_H
+#define PPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppe_plan_s* ppe_plan_t;
+
+typedef enum {
+    PPE_OK = 0,
+    PPE_ERR_INVALID_ARG = 1,
+    PPE_ERR_UNSUPPORTED_SIZE = 2,
+    PPE_ERR_INCOMPATIBLE_RHS = 3,
+    PPE_ERR_OUT_OF_MEMORY = 4,
+    PPE_ERR_NOT_CONVERGED = 5,
+    PPE_ERR_TIMEOUT = 6,
+    PPE_ERR_CUDA = 7
+} ppe_status;
+
+/* Arithmetic of the direct solve.  PPE_FP64: every step in FP64.
+ * PPE_FP32_REFINE: the transforms and the tridiagonal solve run in FP32 inside
+ * an iterative refinement whose residual r = f - L p and solution update are
+ * FP64; the right-hand side and the velocity correction stay FP64. */
+typedef enum { PPE_FP64 = 0, PPE_FP32_REFINE = 1 } ppe_precision;
+
+/* Face density rho_f: arithmetic mean (default) or harmonic mean of the two
+ * adjacent cells.  The paper's face-average rule, Eq. (35), is stated for
+ * interface quantities only; the density rule is a reading of it. */
+typedef enum { PPE_FACE_ARITHMETIC = 0, PPE_FACE_HARMONIC = 1 } ppe_face_rule;
+
+/* Uniform grid, nx x ny x nz cells in a box lx x ly x lz; periodic in x and z,
+ * walls (no penetration, homogeneous Neumann for p) at y = 0 and y = ly. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+} ppe_grid;
+
+typedef struct {
+    ppe_precision precision;
+    ppe_face_rule face_rule;
+    double refine_tol;  /* FP32_REFINE: stop once ||f - L p||_inf <= tol ||f||_inf (e.g. 1e-10) */
+    int max_sweeps;     /* FP32_REFINE: refinement sweeps after the first FP32 solve (<= 16) */
+} ppe_options;
+
+/* Read back by ppe_get_info after a solve or projection. */
+typedef struct {
+    int sweeps;           /* refinement sweeps run (0 for PPE_FP64) */
+    double rel_residual;  /* FP32_REFINE: last ||f - L p||_inf / ||f||_inf measured; -1 for FP64 */
+    double f_max;         /* ||f||_inf of the last right-hand side (-1 if not computed) */
+    double rho0;          /* rho_0 used by the last ppe_rhs / ppe_project */
+} ppe_info;
+
+/* All inputs and outputs of one projection (Eqs. (32)-(34)); device pointers. */
+typedef struct {
+    const double *u, *v, *w;     /* predicted velocity u* on the faces */
+    const double *S;             /* divergence constraint div u^{n+1}, Eq. (31); mean ~ 0 */
+    const double *rho;           /* rho^{n+1} at cell centres, > 0 */
+    const double *p_n, *p_nm1;   /* p^n, p^{n-1} */
+    double rho0;                 /* <= 0: rho_0 = min(rho), computed on the device */
+    double dt;                   /* > 0 */
+    double *p;                   /* out: p^{n+1}, zero mean */
+    double *u_out, *v_out, *w_out; /* out: u^{n+1} (may equal u, v, w) */
+    double *f;                   /* optional out: the Eq. (34) right-hand side, or NULL */
+} ppe_fields;
+
+/* Create a plan: validate sizes, allocate the workspace with cudaMalloc, build
+ * twiddle tables (host FP64, octant-reduced cos/sin) and the tridiagonal
+ * elimination tables for every (kx, kz).  `stream` is a cudaStream_t (NULL =
+ * legacy default stream).  opt may be NULL (FP64, arithmetic faces). */
+ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, void* stream);
+
+/* Re-bind the plan to another stream (for graph capture or serving slots). */
+ppe_status ppe_set_stream(ppe_plan_t plan, void* stream);
+
+/* Bytes of device workspace a plan of this grid and options allocates. */
+size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt);
+
+/* Eq. (34) right-hand side f (device, nx*ny*nz).  rho0 <= 0 selects min(rho). */
+ppe_status ppe_rhs(ppe_plan_t plan, const double* u, const double* v, const double* w,
+                   const double* S, const double* rho, const double* p_n, const double* p_nm1,
+                   double rho0, double dt, double* f);
+
+/* Solve L p = f - mean(f) with mean(p) = 0 (device, nx*ny*nz each).  In
+ * PPE_FP32_REFINE mode this runs the refinement loop on the device. */
+ppe_status ppe_solve(ppe_plan_t plan, const double* f, double* p);
+
+/* Eq. (33) velocity correction.  rho0 <= 0 uses the rho_0 that the last
+ * ppe_rhs or ppe_project on this plan computed on the device. */
+ppe_status ppe_correct(ppe_plan_t plan, const double* u, const double* v, const double* w,
+                       const double* rho, const double* p, const double* p_n, const double* p_nm1,
+                       double rho0, double dt, double* u_out, double* v_out, double* w_out);
+
+/* The whole projection: rho_0, Eq. (34) assembly fused with the forward x
+ * transform, the solve, and Eq. (33).  Same result as rhs + solve + correct. */
+ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
+
+/* ppe_project with HOST input and output arrays (pinned memory recommended):
+ * copies the inputs to plan-owned device buffers (allocated on first use),
+ * projects, and copies p, u, v, w (and f if non-NULL) back.  Synchronises the
+ * plan's stream before returning. */
+ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
+
+/* Synchronise the plan's stream and read the device-side results. */
+ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
+
+/* Free the workspace.  NULL is ignored. */
+void ppe_destroy(ppe_plan_t plan);
+
+/* Per-kernel timing.  While enabled, every kernel the plan launches is
+ * bracketed by two CUDA events on the plan's stream.  ppe_profile_read
+ * synchronises the stream, aggregates the records by kernel into `out`
+ * (at most max_entries), clears them and returns the number of entries
+ * written, or -1 on error.  Adds two event records per launch; meant for
+ * measurement runs, off by default. */
+typedef struct {
+    char name[32];     /* kernel name, e.g. "k_zfft_fwd" */
+    int launches;      /* launches recorded */
+    double total_ms;   /* summed event-to-event time */
+} ppe_kernel_time;
+ppe_status ppe_profile(ppe_plan_t plan, int enable);
+int ppe_profile_read(ppe_plan_t plan, ppe_kernel_time* out, int max_entries);
+
+/* Static text for a status code. */
+const char* ppe_strerror(ppe_status status);
+
+/* Returns 1 if nx, ny, nz are supported by ppe_plan, else 0 (host only). */
+int ppe_size_supported(int nx, int ny, int nz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPE_H */

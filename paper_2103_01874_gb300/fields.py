@@ -108,7 +108,7 @@ def make_fields(nx: int, ny: int, nz: int, *, seed: int = 0, recipe: str = "sing
     else:
         raise ValueError(f"unknown recipe {recipe!r}")
     rho = rho_g + (rho_l - rho_g) * 0.5 * (1.0 - np.tanh(2.0 * (y - eta) / (width * dy)))
-    rho = np.ascontiguousarray(np.broadcast_to(rho, (nz, ny, nx)), dtype=np.float64)
+    rho = np.array(np.broadcast_to(rho, (nz, ny, nx)), dtype=np.float64)  # owned, writable copy
 
     u = rng.standard_normal((nz, ny, nx))
     v = rng.standard_normal((nz, ny + 1, nx))

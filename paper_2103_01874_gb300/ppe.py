@@ -1,0 +1,252 @@
+"""ctypes binding of libppe (include/ppe.h): argument marshalling only.
+
+Every step of the projection runs in the library's CUDA kernels; this module
+checks tensor shapes, dtypes and devices, passes raw device pointers, and
+raises PPEError on a non-zero status.  It loads the in-tree
+paper_2103_01874_gb300/_native/libppe.so and raises RuntimeError if that
+library is missing: there is no host fallback.
+
+Field layout is that of the C ABI: torch float64 tensors, C-contiguous,
+cell fields shaped (nz, ny, nx), v shaped (nz, ny + 1, nx).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_double, c_int, c_size_t, c_void_p
+
+from . import build as _build
+
+FP64 = 0
+FP32_REFINE = 1
+FACE_ARITHMETIC = 0
+FACE_HARMONIC = 1
+
+STATUS = {0: "PPE_OK", 1: "PPE_ERR_INVALID_ARG", 2: "PPE_ERR_UNSUPPORTED_SIZE", 3: "PPE_ERR_INCOMPATIBLE_RHS",
+          4: "PPE_ERR_OUT_OF_MEMORY", 5: "PPE_ERR_NOT_CONVERGED", 6: "PPE_ERR_TIMEOUT", 7: "PPE_ERR_CUDA"}
+
+
+class PPEError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_strerror(code)})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("lx", c_double), ("ly", c_double), ("lz", c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("face_rule", c_int), ("refine_tol", c_double), ("max_sweeps", c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("sweeps", c_int), ("rel_residual", c_double), ("f_max", c_double), ("rho0", c_double)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int), ("total_ms", c_double)]
+
+
+class FieldsC(ctypes.Structure):
+    _fields_ = [("u", c_void_p), ("v", c_void_p), ("w", c_void_p), ("S", c_void_p), ("rho", c_void_p),
+                ("p_n", c_void_p), ("p_nm1", c_void_p), ("rho0", c_double), ("dt", c_double),
+                ("p", c_void_p), ("u_out", c_void_p), ("v_out", c_void_p), ("w_out", c_void_p), ("f", c_void_p)]
+
+
+_LIB = None
+
+# name -> (restype, argtypes), mirroring include/ppe.h
+SIGNATURES = {
+    "ppe_plan": (c_int, [POINTER(c_void_p), POINTER(Grid), POINTER(Options), c_void_p]),
+    "ppe_set_stream": (c_int, [c_void_p, c_void_p]),
+    "ppe_workspace_bytes": (c_size_t, [POINTER(Grid), POINTER(Options)]),
+    "ppe_rhs": (c_int, [c_void_p] + [c_void_p] * 7 + [c_double, c_double, c_void_p]),
+    "ppe_solve": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ppe_correct": (c_int, [c_void_p] + [c_void_p] * 7 + [c_double, c_double] + [c_void_p] * 3),
+    "ppe_project": (c_int, [c_void_p, POINTER(FieldsC)]),
+    "ppe_project_host": (c_int, [c_void_p, POINTER(FieldsC)]),
+    "ppe_get_info": (c_int, [c_void_p, POINTER(Info)]),
+    "ppe_destroy": (None, [c_void_p]),
+    "ppe_strerror": (ctypes.c_char_p, [c_int]),
+    "ppe_size_supported": (c_int, [c_int, c_int, c_int]),
+    "ppe_profile": (c_int, [c_void_p, c_int]),
+    "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libppe.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libppe.so not found at {path}: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().ppe_strerror(code).decode()
+    except Exception:  # pragma: no cover
+        return "?"
+
+
+def size_supported(nx: int, ny: int, nz: int) -> bool:
+    return bool(lib().ppe_size_supported(nx, ny, nz))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise PPEError(code, where)
+
+
+def _ptr(t, shape, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _hptr(a, shape, name):
+    """Host buffer (numpy float64 C-contiguous or pinned torch CPU tensor)."""
+    import numpy as np
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: need a C-contiguous float64 array of shape {shape}")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or a.is_cuda or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name}: need a contiguous float64 CPU tensor of shape {shape}")
+        return a.data_ptr()
+    raise TypeError(name)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A libppe plan for one grid (ppe_plan / ppe_destroy)."""
+
+    def __init__(self, nx, ny, nz, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi, precision=FP64,
+                 face_rule=FACE_ARITHMETIC, refine_tol=1e-10, max_sweeps=6, stream=None):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.lengths = (lx, ly, lz)
+        self.precision = precision
+        self.grid = Grid(nx, ny, nz, lx, ly, lz)
+        self.opts = Options(precision, face_rule, refine_tol, max_sweeps)
+        h = c_void_p()
+        _check(lib().ppe_plan(ctypes.byref(h), ctypes.byref(self.grid), ctypes.byref(self.opts),
+                              c_void_p(_stream_handle(stream))), "ppe_plan")
+        self._h = h
+
+    # shapes
+    @property
+    def cell_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def v_shape(self):
+        return (self.nz, self.ny + 1, self.nx)
+
+    def workspace_bytes(self) -> int:
+        return int(lib().ppe_workspace_bytes(ctypes.byref(self.grid), ctypes.byref(self.opts)))
+
+    def set_stream(self, stream):
+        _check(lib().ppe_set_stream(self._h, c_void_p(_stream_handle(stream))), "ppe_set_stream")
+
+    def rhs(self, u, v, w, S, rho, p_n, p_nm1, dt, f, rho0=-1.0):
+        c, vs = self.cell_shape, self.v_shape
+        _check(lib().ppe_rhs(self._h, _ptr(u, c, "u"), _ptr(v, vs, "v"), _ptr(w, c, "w"), _ptr(S, c, "S"),
+                             _ptr(rho, c, "rho"), _ptr(p_n, c, "p_n"), _ptr(p_nm1, c, "p_nm1"),
+                             float(rho0), float(dt), _ptr(f, c, "f")), "ppe_rhs")
+
+    def solve(self, f, p):
+        c = self.cell_shape
+        _check(lib().ppe_solve(self._h, _ptr(f, c, "f"), _ptr(p, c, "p")), "ppe_solve")
+
+    def correct(self, u, v, w, rho, p, p_n, p_nm1, dt, u_out, v_out, w_out, rho0=-1.0):
+        c, vs = self.cell_shape, self.v_shape
+        _check(lib().ppe_correct(self._h, _ptr(u, c, "u"), _ptr(v, vs, "v"), _ptr(w, c, "w"),
+                                 _ptr(rho, c, "rho"), _ptr(p, c, "p"), _ptr(p_n, c, "p_n"),
+                                 _ptr(p_nm1, c, "p_nm1"), float(rho0), float(dt),
+                                 _ptr(u_out, c, "u_out"), _ptr(v_out, vs, "v_out"), _ptr(w_out, c, "w_out")),
+               "ppe_correct")
+
+    def _fields(self, conv, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
+        c, vs = self.cell_shape, self.v_shape
+        return FieldsC(conv(u, c, "u"), conv(v, vs, "v"), conv(w, c, "w"), conv(S, c, "S"), conv(rho, c, "rho"),
+                       conv(p_n, c, "p_n"), conv(p_nm1, c, "p_nm1"), float(rho0), float(dt), conv(p, c, "p"),
+                       conv(u_out, c, "u_out"), conv(v_out, vs, "v_out"), conv(w_out, c, "w_out"),
+                       conv(f, c, "f"))
+
+    def project(self, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
+        fc = self._fields(_ptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
+        _check(lib().ppe_project(self._h, ctypes.byref(fc)), "ppe_project")
+
+    def project_host(self, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
+        fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
+        _check(lib().ppe_project_host(self._h, ctypes.byref(fc)), "ppe_project_host")
+
+    def info(self, allow_not_converged=False) -> Info:
+        inf = Info()
+        code = lib().ppe_get_info(self._h, ctypes.byref(inf))
+        if code == 5 and allow_not_converged:
+            return inf
+        _check(code, "ppe_get_info")
+        return inf
+
+    def profile(self, enable: bool):
+        _check(lib().ppe_profile(self._h, 1 if enable else 0), "ppe_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total_ms)} since the last read (synchronises)."""
+        buf = (KernelTime * 32)()
+        n = lib().ppe_profile_read(self._h, buf, 32)
+        if n < 0:
+            raise PPEError(7, "ppe_profile_read")
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ppe_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

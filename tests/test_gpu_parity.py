@@ -1,0 +1,170 @@
+"""Parity of the CUDA projection (through the C ABI) with the FP64 oracle.
+
+Bars: FP64 path rel L-inf <= 1e-12 on f, p, u, v, w; FP32 solve + FP64
+refinement: rel residual ||f - L p||_inf / ||f||_inf <= 1e-10 (checked on the
+host in FP64 from the returned f and p), p, u, v, w reported against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ppe_oracle as O
+from paper_2103_01874_gb300 import fields, ppe
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL_RES = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    ppe.lib()
+
+
+def _compare(fl, res, ref, tol, keys=("f", "p", "u", "v", "w")):
+    errs = {k: O.rel_linf(res[k], ref[k]) for k in keys}
+    for k, e in errs.items():
+        assert e <= tol, f"{k}: rel L-inf {e:.3e} > {tol:.1e} ({fl.shape})"
+    return errs
+
+
+SHAPES = [
+    ((32, 32, 32), "single", 2.0, (2 * math.pi,) * 3),
+    ((8, 8, 8), "single", 2.0, (2 * math.pi,) * 3),             # smallest supported
+    ((48, 24, 36), "multimode", 6.0, (2 * math.pi, 3.0, 5.0)),   # anisotropic, ragged CTA tiles
+    ((18, 27, 54), "single", 2.0, (1.0, 2.0, 3.0)),              # radix-3 heavy, odd ny
+    ((96, 16, 12), "multimode", 6.0, (2 * math.pi, 1.0, 0.7)),
+]
+
+
+@pytest.mark.parametrize("shape,recipe,width,lengths", SHAPES)
+def test_project_fp64(shape, recipe, width, lengths):
+    nx, ny, nz = shape
+    fl = fields.make_fields(nx, ny, nz, seed=nx + ny + nz, recipe=recipe, width=width,
+                            lx=lengths[0], ly=lengths[1], lz=lengths[2])
+    ref = O.project_fields(fl)
+    res, info = project_gpu(fl)
+    _compare(fl, res, ref, TOL64)
+    assert info.rho0 == ref["rho0"]
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
+
+
+@pytest.mark.parametrize("rule", [ppe.FACE_ARITHMETIC, ppe.FACE_HARMONIC])
+def test_face_rules_and_given_rho0(rule):
+    fl = fields.make_fields(24, 16, 32, seed=4, recipe="multimode", width=3.0)
+    ref = O.project_fields(fl, rule=rule, rho0=100.0)
+    res, info = project_gpu(fl, face_rule=rule, rho0=100.0)
+    _compare(fl, res, ref, TOL64)
+    assert info.rho0 == 100.0
+
+
+def test_separate_entry_points_match_project():
+    """ppe_rhs -> ppe_solve -> ppe_correct (in place) equals the oracle."""
+    import torch
+    fl = fields.make_fields(32, 24, 16, seed=8, recipe="multimode", width=4.0)
+    ref = O.project_fields(fl)
+    d = dev_fields(fl)
+    f = torch.empty(fl.shape, dtype=torch.float64, device="cuda")
+    p = torch.empty_like(f)
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz) as plan:
+        plan.rhs(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, f)
+        plan.solve(f, p)
+        plan.correct(d["u"], d["v"], d["w"], d["rho"], p, d["p_n"], d["p_nm1"], fl.dt, d["u"], d["v"], d["w"])
+        torch.cuda.synchronize()
+    res = dict(f=f.cpu().numpy(), p=p.cpu().numpy(), u=d["u"].cpu().numpy(), v=d["v"].cpu().numpy(),
+               w=d["w"].cpu().numpy())
+    _compare(fl, res, ref, TOL64)
+
+
+def test_solve_manufactured_eigenfunction():
+    """The GPU solve of lam * phi returns phi for a discrete eigenfunction."""
+    import torch
+    nz, ny, nx = 24, 12, 16
+    L = (2 * math.pi, 3.0, 5.0)
+    dx, dy, dz = L[0] / nx, L[1] / ny, L[2] / nz
+    a, b, c = 3, 2, 5
+    x = (np.arange(nx) + 0.5) * dx
+    z = (np.arange(nz) + 0.5) * dz
+    phi = (np.cos(2 * math.pi * a * x / L[0] + 0.3)[None, None, :] * np.cos(math.pi * b * (np.arange(ny) + 0.5) / ny)
+           [None, :, None] * np.cos(2 * math.pi * c * z / L[2] - 1.1)[:, None, None])
+    lam = (-(4 / dx**2) * math.sin(math.pi * a / nx) ** 2 - (4 / dy**2) * math.sin(math.pi * b / (2 * ny)) ** 2
+           - (4 / dz**2) * math.sin(math.pi * c / nz) ** 2)
+    f = to_dev(lam * phi)
+    p = torch.empty_like(f)
+    with ppe.Plan(nx, ny, nz, *L) as plan:
+        plan.solve(f, p)
+    assert O.rel_linf(p.cpu().numpy(), phi) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 24, 36)])
+def test_project_fp32_refine(shape):
+    nx, ny, nz = shape
+    fl = fields.make_fields(nx, ny, nz, seed=3, recipe="multimode", width=6.0, rho_g=60.0)
+    ref = O.project_fields(fl)
+    res, info = project_gpu(fl, precision=ppe.FP32_REFINE)
+    L = (fl.lx, fl.ly, fl.lz)
+    r = O.residual(res["f"], res["p"], L)
+    rel = np.abs(r - r.mean()).max() / np.abs(res["f"]).max()
+    assert rel <= TOL_RES, rel
+    assert info.rel_residual <= TOL_RES
+    assert O.rel_linf(res["f"], ref["f"]) <= TOL64
+    for k in ("p", "u", "v", "w"):
+        assert O.rel_linf(res[k], ref[k]) <= 1e-8, k
+
+
+def test_project_128_fp64_full():
+    """The 128^3 multimode workload, whole-field comparison."""
+    fl = fields.multimode_128()
+    ref = O.project_fields(fl)
+    res, _ = project_gpu(fl)
+    _compare(fl, res, ref, TOL64)
+
+
+def test_project_256_fp32_refine_full():
+    """The 256^3, density ratio 640/60 workload in the mixed-precision form."""
+    fl = fields.multimode_256()
+    ref = O.project_fields(fl)
+    res, info = project_gpu(fl, precision=ppe.FP32_REFINE)
+    r = O.residual(res["f"], res["p"], (fl.lx, fl.ly, fl.lz))
+    rel = np.abs(r - r.mean()).max() / np.abs(res["f"]).max()
+    assert rel <= TOL_RES, rel
+    assert O.rel_linf(res["f"], ref["f"]) <= TOL64
+    for k in ("p", "u", "v", "w"):
+        assert O.rel_linf(res[k], ref[k]) <= 1e-8, k
+
+
+def test_project_host_buffers():
+    fl = fields.make_fields(32, 16, 24, seed=12, recipe="single")
+    ref = O.project_fields(fl)
+    c = fl.shape
+    out = dict(p=np.empty(c), u=np.empty(c), v=np.empty(fl.v.shape), w=np.empty(c), f=np.empty(c))
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz) as plan:
+        plan.project_host(fl.u, fl.v, fl.w, fl.S, fl.rho, fl.p_n, fl.p_nm1, fl.dt, out["p"], out["u"], out["v"],
+                          out["w"], f=out["f"])
+    _compare(fl, out, ref, TOL64)
+
+
+def test_errors():
+    import torch
+    with pytest.raises(ppe.PPEError) as e:
+        ppe.Plan(250, 32, 32)
+    assert e.value.code == 2
+    with pytest.raises(ppe.PPEError) as e:
+        ppe.Plan(9, 32, 32)  # odd nx
+    assert e.value.code == 2
+    with ppe.Plan(8, 8, 8) as plan:
+        f = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(ValueError):
+            plan.solve(f.float(), f)
+        d = {k: torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda") for k in "uwSrab"}
+        v = torch.zeros((8, 9, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(ppe.PPEError) as e:
+            plan.rhs(d["u"], v, d["w"], d["S"], d["r"], d["a"], d["b"], 0.0, f)
+        assert e.value.code == 1
+
+
+from _gpu_util import dev_fields, project_gpu, to_dev  # noqa: E402
