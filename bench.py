@@ -39,6 +39,14 @@ N_CELLS = NX * NY * NZ
 F_BYTES = 8 * N_CELLS
 
 
+def set_grid(n: int):
+    """Grid edge for profiling runs of a smaller case (the bench line itself is 256^3)."""
+    global NX, NY, NZ, N_CELLS, F_BYTES
+    NX = NY = NZ = n
+    N_CELLS = n ** 3
+    F_BYTES = 8 * N_CELLS
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -118,15 +126,17 @@ def kernel_bytes(kernel: str, fp32: bool) -> float:
     Fv = F * (NY + 1) / NY
     spec = (NX // 2 + 1) * NY * NZ * (8 if fp32 else 16)
     table = {
-        "k_xfwd_rhs": 6 * F + Fv + (F if fp32 else 0) + spec,   # 7 inputs; f kept (refine); spectrum
+        # 7 FP64 inputs; u_pre on all faces (float pairs); f as pairs (refinement); half spectrum
+        "k_rhs_march": 6 * F + Fv + (2 * F + Fv) + (F if fp32 else 0) + spec,
         "k_xfwd_f": F + spec,
-        "k_xfwd_resid": 2 * F + spec,                           # f, p -> spectrum
+        "k_xfwd_resid": 2 * F + spec,                   # f, p (pairs) -> spectrum
         "k_zfft_fwd": 2 * spec,
         "k_ythomas": 2 * spec,
         "k_zfft_inv": 2 * spec,
-        "k_xinv": spec + F,
-        "k_xinv_accum": spec + 2 * F,
-        "k_correct": 6 * F + Fv + F + 2 * F + Fv,               # u*,v*,w*,rho,p^n,p^{n-1},p ; u,v,w
+        "k_xinv": spec + F,                             # -> p (FP64 or pairs)
+        "k_xinv_accum": spec + 2 * F,                   # p += delta (pairs)
+        # u_pre + p in, u, v, w (+ p FP64 for the refinement form) out
+        "k_correct": (2 * F + Fv) + F + (2 * F + Fv) + (F if fp32 else 0),
         "k_rho_min": F,
     }
     return table.get(kernel, 0.0)
@@ -159,7 +169,10 @@ def run_gpu(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    fl = fields.multimode_256(seed=2 + rank)
+    if NX == 256:
+        fl = fields.multimode_256(seed=2 + rank)
+    else:
+        fl = fields.make_fields(NX, NY, NZ, seed=2 + rank, recipe="multimode", width=6.0, rho_g=60.0)
     d = {k: torch.from_numpy(v).to(dev) for k, v in fl.arrays().items()}
     c = fl.shape
     out = dict(p=torch.empty(c, dtype=torch.float64, device=dev), u=torch.empty_like(d["u"]),
@@ -200,6 +213,7 @@ def run_gpu(args):
         return ms, kt
 
     steps, warmup = args.steps, args.warmup
+    forms = set(args.forms.split(","))
     plan32 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, refine_tol=1e-10,
                       max_sweeps=args.max_sweeps, stream=stream)
     with ClockSampler(dev.index if world > 1 else 0) as clk:
@@ -207,12 +221,15 @@ def run_gpu(args):
     clocks = clk.summary()
     info32 = plan32.info(allow_not_converged=True)
     # per-kernel event timing over a second timed region of the same steps
-    ms32p, kt32 = timed(plan32, steps, 1, profile=True)
+    ms32p, kt32 = timed(plan32, steps, 1, profile=True) if args.kernel_times else (0.0, {})
 
-    plan64 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP64, stream=stream)
-    ms64, _ = timed(plan64, max(1, steps // 2), max(3, warmup // 2))
     steps64 = max(1, steps // 2)
-    ms64p, kt64 = timed(plan64, steps64, 1, profile=True)
+    ms64, kt64 = 0.0, {}
+    if "fp64" in forms:
+        plan64 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP64, stream=stream)
+        ms64, _ = timed(plan64, steps64, max(3, warmup // 2))
+        if args.kernel_times:
+            _, kt64 = timed(plan64, steps64, 1, profile=True)
 
     # e2e: the same projection from pinned host buffers through ppe_project_host
     hin = {k: torch.from_numpy(v).pin_memory() for k, v in fl.arrays().items()}
@@ -225,15 +242,17 @@ def run_gpu(args):
         plan32.project_host(hin["u"], hin["v"], hin["w"], hin["S"], hin["rho"], hin["p_n"], hin["p_nm1"], fl.dt,
                             hout["p"], hout["u"], hout["v"], hout["w"])
 
-    for _ in range(2):
-        host_step()
-    barrier()
     e_steps = max(2, steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        host_step()
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = float("nan")
+    if not args.no_e2e:
+        for _ in range(2):
+            host_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            host_step()
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
     if dist is not None:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -290,9 +309,10 @@ def run_gpu(args):
         "step_roofline": {"min_pass_bytes": step_bytes, "achieved_GBps": step_bytes / (per_step32 * 1e-3) / 1e9,
                           "frac_of_hbm": step_bytes / (per_step32 * 1e-3) / 1e9 / hbm},
         "fp64": {"solves_per_s": world * steps64 / (ms64 * 1e-3) if ms64 else None,
-                 "ms_per_step": ms64 / max(1, steps // 2),
-                 "gpts_per_s": world * steps64 / (ms64 * 1e-3) * N_CELLS / 1e9,
-                 "step_min_pass_frac_of_hbm": step_min_bytes(False, 0) / (ms64 / steps64 * 1e-3) / 1e9 / hbm,
+                 "ms_per_step": ms64 / steps64 if ms64 else None,
+                 "gpts_per_s": world * steps64 / (ms64 * 1e-3) * N_CELLS / 1e9 if ms64 else None,
+                 "step_min_pass_frac_of_hbm": (step_min_bytes(False, 0) / (ms64 / steps64 * 1e-3) / 1e9 / hbm
+                                               if ms64 else None),
                  "kernels": kernels64},
         "roofline": roof,
         "kernels": kernels,
@@ -386,7 +406,12 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=8)
     ap.add_argument("--cpu-solves", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=256, help="grid edge (profiling runs only; the bench line is 256)")
+    ap.add_argument("--forms", default="fp32,fp64", help="fp32 (always) and/or fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernel-times", dest="kernel_times", action="store_false")
     args = ap.parse_args()
+    set_grid(args.n)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -1,0 +1,190 @@
+// Double-float ("float-float") arithmetic and exact-ish FP64 <-> pair
+// conversions done with integer operations.
+//
+// Why: on a GB300 an FP64 FMA, and also every f64<->f32 conversion, issues at
+// about 1/64 of the FP32 rate (measured: 1.19 TFLOP/s FP64 against 72.9 FP32;
+// cvt f64<->f32 at ~1.9 per clock per SM; cvt u32->f32 at ~34).  The stencils
+// of the projection (Eq. (34) right-hand side, the residual f - L p of the
+// refinement, Eq. (33) correction) need FP64-level accuracy but few ops per
+// byte, so they read and write IEEE FP64 at the API boundary and compute on
+// pairs (hi, lo) of floats carrying ~48 significant bits.
+//
+// Published methods used (restated, not copied):
+//   * TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and FastTwoSum (Dekker 1971) give
+//     a + b = s + e exactly;
+//   * TwoProd with a fused multiply-add (as in Dekker 1971 / the FMA
+//     formulation of Ogita, Rump and Oishi 2005) gives a * b = p + e exactly;
+//   * one Newton-Raphson step y1 = y0 + y0 (1 - a y0) for the reciprocal.
+//
+// Representation: value = hi + lo, |lo| <= ulp(hi)/2 after normalisation.
+// Relative precision ~2^-48 (3.6e-15).  Range: magnitudes in [2^-74, 2^127];
+// smaller inputs are flushed to zero (their contribution is below 1e-22 in
+// absolute value), larger ones are out of scope.
+//
+// d2df(x): hi = x truncated to 24 significant bits (exponent rebias and
+// mantissa shift on the bit pattern), lo = the remaining 29 mantissa bits as an
+// integer, converted with one int->float conversion and scaled by 2^(e-1075).
+// df2d(a): exact double of hi from its bits, plus lo expressed in units of the
+// double ulp of hi (a float scaling by a power of two and one float->int
+// conversion) added to the bit pattern.  Both use only integer and FP32 ops.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#ifdef __CUDACC__
+#define PPE_HD __host__ __device__ __forceinline__
+#else
+#define PPE_HD inline
+#endif
+
+namespace ppe {
+
+struct df {
+  float hi, lo;
+};
+
+PPE_HD uint32_t f_bits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+PPE_HD float f_from(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+PPE_HD uint64_t d_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+PPE_HD double d_from(uint64_t u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+PPE_HD float rcp_rn(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+PPE_HD int f2i_rn(float x) {
+#ifdef __CUDA_ARCH__
+  return __float2int_rn(x);
+#else
+  return (int)lrintf(x);
+#endif
+}
+
+// a + b = s + e exactly (any magnitudes)
+PPE_HD df two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+// a + b = s + e exactly when |a| >= |b| (or a == 0)
+PPE_HD df fast_two_sum(float a, float b) {
+  const float s = a + b;
+  const float e = b - (s - a);
+  return {s, e};
+}
+// a * b = p + e exactly
+PPE_HD df two_prod(float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  return {p, e};
+}
+
+PPE_HD df df_make(float x) { return {x, 0.0f}; }
+PPE_HD df df_neg(df a) { return {-a.hi, -a.lo}; }
+PPE_HD df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+PPE_HD df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+PPE_HD df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  s.lo += a.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+PPE_HD df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+PPE_HD df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = fmaf(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+// exact scaling by a power of two
+PPE_HD df df_ldexp2(df a) { return {2.0f * a.hi, 2.0f * a.lo}; }
+// 1/a: correctly rounded float seed, one Newton step carried in pairs
+PPE_HD df df_recip(df a) {
+  const float y0 = rcp_rn(a.hi);
+  df p = two_prod(a.hi, y0);                  // a.hi*y0 = p.hi + p.lo exactly, p.hi ~ 1
+  const float e = ((1.0f - p.hi) - p.lo) - a.lo * y0;  // 1 - a*y0 to float precision
+  return fast_two_sum(y0, y0 * e);
+}
+PPE_HD float df_to_f(df a) { return a.hi + a.lo; }
+
+// IEEE double -> pair (see header comment).  Relative error <= 2^-48.
+PPE_HD df d2df(double x) {
+  const uint64_t b = d_bits(x);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const uint32_t e = (hw >> 20) & 0x7FFu;
+  const uint32_t sign = hw & 0x80000000u;
+  // hi: rebias 1023 -> 127 and keep the top 23 mantissa bits
+  const uint32_t hb = sign | (((hw & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lw >> 29);
+  // lo: 29 low mantissa bits times 2^(e - 1075)
+  const float m = (float)(lw & 0x1FFFFFFFu);
+  const float sc = f_from((e - 948u) << 23);
+  const float lo = f_from(f_bits(m * sc) | sign);
+  df r;
+  r.hi = (e >= 897u) ? f_from(hb) : 0.0f;
+  r.lo = (e >= 949u) ? lo : 0.0f;
+  return r;
+}
+
+// pair -> IEEE double (see header comment).  Relative error ~2^-53.
+PPE_HD double df2d(df a) {
+  a = fast_two_sum(a.hi, a.lo);
+  const uint32_t hb = f_bits(a.hi);
+  const uint32_t eh = (hb >> 23) & 0xFFu;  // biased float exponent of hi
+  if (eh == 0u) return 0.0;                // |hi| < 2^-126: flushed
+  // exact double of hi: rebias 127 -> 1023, mantissa to the top of 52 bits
+  const uint64_t Hb = ((uint64_t)(hb >> 31) << 63) | ((uint64_t)(eh + 896u) << 52) |
+                      ((uint64_t)(hb & 0x7FFFFFu) << 29);
+  // lo in units of the double ulp of hi, 2^(E_h - 52) with E_h = eh - 127;
+  // a negative lo below a power of two counts in the next binade down
+  const bool down = ((hb & 0x7FFFFFu) == 0u) && ((a.lo < 0.0f) != (a.hi < 0.0f)) && a.lo != 0.0f;
+  const uint32_t se = (down ? 307u : 306u) - eh;  // biased exponent of 2^(52 - E_h) (+1 if down)
+  if (se >= 255u || se == 0u) return d_from(Hb);
+  const float sc = f_from(se << 23);
+  int k = f2i_rn(a.lo * sc);
+  if (a.hi < 0.0f) k = -k;  // the bit pattern counts magnitude
+  return d_from((uint64_t)((int64_t)Hb + (int64_t)k));
+}
+
+}  // namespace ppe

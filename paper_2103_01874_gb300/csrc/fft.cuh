@@ -16,6 +16,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "fastdiv.cuh"
+
 namespace ppe {
 
 template <typename T> struct cpx { T x, y; };
@@ -37,11 +39,13 @@ __device__ __forceinline__ cpx<T> rot(cpx<T> a) {
   return INV ? cpx<T>{-a.y, a.x} : cpx<T>{a.y, -a.x};
 }
 
-// Radices applied in order; n = prod r[s].
+// Radices applied in order; n = prod r[s]; ns[s] divides by the product of
+// the radices before stage s.
 struct RadixPlan {
   int n;
   int nst;
   int r[16];
+  FastDiv ns[16];
 };
 
 template <typename T, bool INV, int R> struct SmallDft;
@@ -80,27 +84,35 @@ template <typename T, bool INV> struct SmallDft<T, INV, 4> {
   }
 };
 
-// One Stockham pass.  Line `l`, element `e` lives at base[l*ls + e*es].  With
+// One Stockham pass over nl = 2^nl_log2 lines (nl <= blockDim.x, blockDim.x a
+// power of two).  Line `l`, element `e` lives at base[l*ls + e*es].  With
 // line_fastest, consecutive threads take consecutive lines (suits lines that
-// are interleaved in memory, es > 1); otherwise consecutive butterflies.
+// are interleaved in memory, es > 1); otherwise each line gets blockDim/nl
+// consecutive threads.  No integer division: shifts, masks and a
+// multiply-high divider for Ns.
 template <typename T, bool INV, int R>
-__device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
-                                              int nl, int n, int ls, int es, int Ns,
+__device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst, int nl_log2,
+                                              int n, int ls, int es, int Ns, const FastDiv& nsdiv,
                                               const cpx<T>* __restrict__ tw, int tws, bool line_fastest) {
   const int nb = n / R;
-  const int total = nl * nb;
   const int tstep = n / (Ns * R);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    int line, t;
-    if (line_fastest) {
-      line = idx % nl;
-      t = idx / nl;
-    } else {
-      t = idx % nb;
-      line = idx / nb;
-    }
-    const int k = t % Ns;
-    const cpx<T>* s = src + line * ls;
+  const int bl = __ffs(blockDim.x) - 1;
+  int line, t0, ts;
+  if (line_fastest) {
+    line = threadIdx.x & ((1 << nl_log2) - 1);
+    t0 = threadIdx.x >> nl_log2;
+    ts = blockDim.x >> nl_log2;
+  } else {
+    const int tl = bl - nl_log2;  // log2 threads per line
+    line = threadIdx.x >> tl;
+    t0 = threadIdx.x & ((1 << tl) - 1);
+    ts = 1 << tl;
+  }
+  const cpx<T>* s = src + line * ls;
+  cpx<T>* d = dst + line * ls;
+  for (int t = t0; t < nb; t += ts) {
+    const int q0 = (int)fdiv((uint32_t)t, nsdiv);
+    const int k = t - q0 * Ns;
     cpx<T> v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = s[(t + q * nb) * es];
@@ -114,29 +126,28 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
       }
     }
     SmallDft<T, INV, R>::run(v);
-    cpx<T>* d = dst + line * ls;
-    const int base = (t / Ns) * Ns * R + k;
+    const int base = q0 * Ns * R + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) d[(base + q * Ns) * es] = v[q];
   }
 }
 
-// Full transform of nl lines held in `a` (with `b` as the second buffer).
-// The caller synchronises before the call; the routine synchronises after
-// every pass and returns the buffer that holds the result.  `tw` is the table
-// exp(-2 pi i t / (n*tws)), t < n*tws.
+// Full transform of 2^nl_log2 lines held in `a` (with `b` as the second
+// buffer).  The caller synchronises before the call; the routine synchronises
+// after every pass and returns the buffer that holds the result.  `tw` is the
+// table exp(-2 pi i t / (n*tws)), t < n*tws.
 template <typename T, bool INV>
-__device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, int nl, const RadixPlan& rp, int ls, int es,
+__device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, int nl_log2, const RadixPlan& rp, int ls, int es,
                              const cpx<T>* __restrict__ tw, int tws, bool line_fastest) {
   int Ns = 1;
   for (int s = 0; s < rp.nst; ++s) {
     const int R = rp.r[s];
     if (R == 4)
-      stockham_pass<T, INV, 4>(a, b, nl, rp.n, ls, es, Ns, tw, tws, line_fastest);
+      stockham_pass<T, INV, 4>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
     else if (R == 2)
-      stockham_pass<T, INV, 2>(a, b, nl, rp.n, ls, es, Ns, tw, tws, line_fastest);
+      stockham_pass<T, INV, 2>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
     else
-      stockham_pass<T, INV, 3>(a, b, nl, rp.n, ls, es, Ns, tw, tws, line_fastest);
+      stockham_pass<T, INV, 3>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
     __syncthreads();
     cpx<T>* t = a;
     a = b;

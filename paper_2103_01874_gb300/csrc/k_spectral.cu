@@ -5,14 +5,19 @@
 // kx = 0 .. nx/2 (nxh = nx/2 + 1 values, the real-input half spectrum), j the
 // physical wall-normal index, kz = 0 .. nz-1.  Every pass works in place.
 //
-//   k_xfwd    one CTA per `lpb` x-lines: builds the real line (Eq. (34) RHS,
-//             a given f, or the residual f - L p), packs it as nx/2 complex
-//             values, FFTs them and untangles the nx/2+1 half spectrum.
+//   k_xfwd    one CTA per `lpb` x-lines: builds the real line (a given f, or
+//             the residual f - L p of the refinement in pair arithmetic), packs
+//             it as nx/2 complex values, FFTs them and untangles the nx/2+1
+//             half spectrum.  (The Eq. (34) right-hand side has its own fused
+//             kernel, k_rhs.cu.)
 //   k_zfft    one CTA per (j, tile of `tkx` kx columns): FFT along z.
 //   k_ythomas one thread per (kx, kz): the Neumann tridiagonal solve in y with
 //             precomputed elimination multipliers; zero mode pinned.
 //   k_xinv    one CTA per `lpb` lines: half spectrum -> real line, scaled, and
-//             stored to p or added to p (refinement update).
+//             stored to p (FP64), stored as pairs, or added to the pairs
+//             (refinement update).
+#include "async.cuh"
+#include "dfloat.cuh"
 #include "ppe_internal.h"
 #include "stencil.cuh"
 
@@ -23,49 +28,64 @@ __device__ __forceinline__ cpx<T> ld_tw(const cpx<T>* tw, int t) {
   return tw[t];
 }
 
+// log2 of a power of two
+__device__ __forceinline__ int ilog2_dev(int v) { return __ffs(v) - 1; }
+
 // ---------------------------------------------------------------------------
 // forward x pass
 // ---------------------------------------------------------------------------
 template <typename T, int SRC, bool DO_FFT>
-__global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, double* f_out,
-                                              cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb) {
+__global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                              const df* __restrict__ pdf, cpx<T>* spec, RadixPlan rp,
+                                              const cpx<T>* __restrict__ tw, int lpb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (SRC == SRC_RESID && sc->done) return;
+  if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
   const int nlines = g.ny * g.nz;
   const int l0 = blockIdx.x * lpb;
   T* line_re = reinterpret_cast<T*>(smem_raw);                       // lpb * nx reals == lpb * M complex
   cpx<T>* bufb = reinterpret_cast<cpx<T>*>(smem_raw + sizeof(T) * (size_t)lpb * nx);
 
-  double rho0 = 0.0;
-  if (SRC == SRC_RHS) rho0 = read_rho0(sc);
-  double vmax = 0.0;
-  for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
-    const int ll = idx / nx, i = idx - ll * nx;
-    const int line = l0 + ll;
-    double val = 0.0;
-    if (line < nlines) {
-      const int k = line / g.ny, j = line - k * g.ny;
-      if (SRC == SRC_RHS) {
-        val = rhs_at(g, in, rho0, i, j, k);
-        if (f_out) f_out[(size_t)line * nx + i] = val;
-      } else if (SRC == SRC_F) {
-        val = __ldg(in.f + (size_t)line * nx + i);
-      } else {
-        val = resid_at(g, in, i, j, k);
-      }
-      vmax = fmax(vmax, fabs(val));
-    }
-    line_re[idx] = (T)val;
+  df lc[3];
+  if (SRC == SRC_RESID) {
+    lc[0] = sc->K.lx;
+    lc[1] = sc->K.ly;
+    lc[2] = sc->K.lz;
   }
-  if (SRC == SRC_RHS || SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
-  else block_max_to(&sc->rmax_bits[slot], vmax);
+  float vmax = 0.0f;
+  for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
+    const int ll = (int)fdiv(idx, g.fd_nx), i = idx - ll * nx;
+    const int line = l0 + ll;
+    T val = (T)0;
+    if (line < nlines) {
+      const size_t c = (size_t)line * nx + i;
+      if (SRC == SRC_F) {
+        const double x = __ldg(in.f + c);
+        if (sizeof(T) == 8) {
+          val = (T)x;
+        } else {
+          const df v = d2df(x);
+          if (fdf) fdf[c] = v;
+          val = (T)df_to_f(v);
+        }
+        vmax = fmaxf(vmax, fabsf(d2df(x).hi));
+      } else {
+        const int k = (int)fdiv(line, g.fd_ny), j = line - k * g.ny;
+        const df r = resid_df(g, fdf, pdf, lc, i, j, k);
+        val = (T)df_to_f(r);
+        vmax = fmaxf(vmax, fabsf(r.hi));
+      }
+    }
+    line_re[idx] = val;
+  }
+  if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
+  else block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
   if (!DO_FFT) return;
   __syncthreads();
-  cpx<T>* z = fft_lines<T, false>(reinterpret_cast<cpx<T>*>(line_re), bufb, lpb, rp, M, 1, tw, 2, false);
+  cpx<T>* z = fft_lines<T, false>(reinterpret_cast<cpx<T>*>(line_re), bufb, ilog2_dev(lpb), rp, M, 1, tw, 2, false);
   // untangle: X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, W = exp(-2 pi i/nx)
   for (int idx = threadIdx.x; idx < lpb * nxh; idx += blockDim.x) {
-    const int ll = idx / nxh, kx = idx - ll * nxh;
+    const int ll = (int)fdiv(idx, g.fd_nxh), kx = idx - ll * nxh;
     const int line = l0 + ll;
     if (line >= nlines) continue;
     const cpx<T> zk = z[ll * M + (kx == M ? 0 : kx)];
@@ -96,16 +116,19 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
   cpx<T>* b = a + (size_t)tkx * nz;
   const size_t rowstride = (size_t)g.ny * nxh;
   const size_t base = (size_t)j * nxh + kx0;
+  const int tl2 = ilog2_dev(tkx);
   for (int idx = threadIdx.x; idx < nz * tkx; idx += blockDim.x) {
-    const int k = idx / tkx, c = idx - k * tkx;
-    cpx<T> v = {(T)0, (T)0};
-    if (kx0 + c < nxh) v = spec[base + k * rowstride + c];
-    a[idx] = v;
+    const int k = idx >> tl2, c = idx & (tkx - 1);
+    if (kx0 + c < nxh)
+      cp_async<sizeof(cpx<T>)>(&a[idx], &spec[base + k * rowstride + c]);
+    else
+      a[idx] = {(T)0, (T)0};
   }
+  cp_async_wait_all();
   __syncthreads();
-  cpx<T>* r = fft_lines<T, INV>(a, b, tkx, rp, 1, tkx, tw, 1, true);
+  cpx<T>* r = fft_lines<T, INV>(a, b, tl2, rp, 1, tkx, tw, 1, true);
   for (int idx = threadIdx.x; idx < nz * tkx; idx += blockDim.x) {
-    const int k = idx / tkx, c = idx - k * tkx;
+    const int k = idx >> tl2, c = idx & (tkx - 1);
     if (kx0 + c < nxh) spec[base + k * rowstride + c] = r[idx];
   }
 }
@@ -124,70 +147,102 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
 // bit for bit for J <= j <= N-2.  For kx = kz = 0 the matrix is singular (the
 // constant mode): m_0 = 0 pins x_0 = 0, the mean of d is removed first and the
 // mean of x afterwards, which gives the zero-mean solution.
+// One CTA per tile of `tl` consecutive kx lines at one kz: the tile (all j) is
+// copied to shared memory with asynchronous copies, the tl multiplier tables are
+// gathered into shared memory, one thread per line runs both sweeps in shared
+// memory, and the tile is written back.
 template <typename T>
 __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const T* __restrict__ tab,
                                                  const int* __restrict__ line_off, const int* __restrict__ line_len,
-                                                 T a, const DevScalars* sc) {
+                                                 T a, int tl, const DevScalars* sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
   const int nxh = g.nx / 2 + 1, ny = g.ny;
-  const int line = blockIdx.x * blockDim.x + threadIdx.x;
-  if (line >= nxh * g.nz) return;
-  const int kx = line % nxh, kz = line / nxh;
-  cpx<T>* d = spec + (size_t)kz * ny * nxh + kx;
-  const size_t st = nxh;
-  const int off = line_off[line], J = line_len[line];
-  const T m_inf = tab[off], m_last = tab[off + 1];
-  const T* mj = tab + off + 2;
-  cpx<T> shift = {(T)0, (T)0};
-  if (line == 0) {
-    double sx = 0.0, sy = 0.0;
-    for (int j = 0; j < ny; ++j) {
-      sx += (double)d[j * st].x;
-      sy += (double)d[j * st].y;
-    }
-    shift.x = (T)(sx / ny);
-    shift.y = (T)(sy / ny);
+  const int ntile = (nxh + tl - 1) / tl;
+  const int kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * tl;
+  cpx<T>* d = reinterpret_cast<cpx<T>*>(smem_raw);      // [ny][tl]
+  T* tm = reinterpret_cast<T*>(d + (size_t)ny * tl);     // [tl][ny + 1]
+  const size_t base = (size_t)kz * ny * nxh + kx0;
+  const int tl2 = ilog2_dev(tl);
+  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
+    const int j = idx >> tl2, c = idx & (tl - 1);
+    if (kx0 + c < nxh)
+      cp_async<sizeof(cpx<T>)>(&d[idx], &spec[base + (size_t)j * nxh + c]);
+    else
+      d[idx] = {(T)0, (T)0};
   }
-  cpx<T> prev = {(T)0, (T)0};
-  for (int j = 0; j < ny; ++j) {
-    const T m = (j < J) ? mj[j] : ((j < ny - 1) ? m_inf : m_last);
-    cpx<T> v = d[j * st];
-    v.x = (v.x - shift.x - a * prev.x) * m;
-    v.y = (v.y - shift.y - a * prev.y) * m;
-    d[j * st] = v;
-    prev = v;
-  }
-  for (int j = ny - 2; j >= 0; --j) {
-    const T m = (j < J) ? mj[j] : m_inf;
-    const T c = a * m;
-    cpx<T> v = d[j * st];
-    v.x -= c * prev.x;
-    v.y -= c * prev.y;
-    d[j * st] = v;
-    prev = v;
-  }
-  if (line == 0) {
-    double sx = 0.0, sy = 0.0;
-    for (int j = 0; j < ny; ++j) {
-      sx += (double)d[j * st].x;
-      sy += (double)d[j * st].y;
+  // multipliers m_j of each line: stored entries, then m_inf, and m_last at j = ny-1
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
+    const int c = (int)fdiv(idx, g.fd_ny), j = idx - c * ny;
+    T m = (T)0;
+    if (kx0 + c < nxh) {
+      const int line = kz * nxh + kx0 + c;
+      const int off = line_off[line], J = line_len[line];
+      m = (j < J) ? tab[off + 2 + j] : ((j < ny - 1) ? tab[off] : tab[off + 1]);
     }
-    const T mx = (T)(sx / ny), my = (T)(sy / ny);
-    for (int j = 0; j < ny; ++j) {
-      cpx<T> v = d[j * st];
-      v.x -= mx;
-      v.y -= my;
-      d[j * st] = v;
+    tm[c * (ny + 1) + j] = m;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < tl && kx0 + c < nxh) {
+    const T* m = tm + c * (ny + 1);
+    const bool zero_line = (kz == 0 && kx0 + c == 0);
+    cpx<T> shift = {(T)0, (T)0};
+    if (zero_line) {
+      double sx = 0.0, sy = 0.0;
+      for (int j = 0; j < ny; ++j) {
+        sx += (double)d[j * tl + c].x;
+        sy += (double)d[j * tl + c].y;
+      }
+      shift.x = (T)(sx / ny);
+      shift.y = (T)(sy / ny);
     }
+    cpx<T> prev = {(T)0, (T)0};
+    for (int j = 0; j < ny; ++j) {
+      const T mj = m[j];
+      cpx<T> v = d[j * tl + c];
+      v.x = (v.x - shift.x - a * prev.x) * mj;
+      v.y = (v.y - shift.y - a * prev.y) * mj;
+      d[j * tl + c] = v;
+      prev = v;
+    }
+    for (int j = ny - 2; j >= 0; --j) {
+      const T cj = a * m[j];
+      cpx<T> v = d[j * tl + c];
+      v.x -= cj * prev.x;
+      v.y -= cj * prev.y;
+      d[j * tl + c] = v;
+      prev = v;
+    }
+    if (zero_line) {
+      double sx = 0.0, sy = 0.0;
+      for (int j = 0; j < ny; ++j) {
+        sx += (double)d[j * tl + c].x;
+        sy += (double)d[j * tl + c].y;
+      }
+      const T mx = (T)(sx / ny), my = (T)(sy / ny);
+      for (int j = 0; j < ny; ++j) {
+        d[j * tl + c].x -= mx;
+        d[j * tl + c].y -= my;
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
+    const int j = idx >> tl2, cc = idx & (tl - 1);
+    if (kx0 + cc < nxh) spec[base + (size_t)j * nxh + cc] = d[idx];
   }
 }
 
 // ---------------------------------------------------------------------------
 // inverse x pass
 // ---------------------------------------------------------------------------
-template <typename T, bool ACCUM>
-__global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, double scale,
-                                              RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
+// MODE: XI_F64 p = s x (FP64); XI_DF pdf = s x (pairs); XI_DF_ACC pdf += s x
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, df* pdf,
+                                              double scale, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
                                               const DevScalars* sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
@@ -197,16 +252,18 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb * M
   cpx<T>* b = a + (size_t)lpb * M;                  // lpb * (M + 1)
   for (int idx = threadIdx.x; idx < lpb * nxh; idx += blockDim.x) {
-    const int ll = idx / nxh;
+    const int ll = (int)fdiv(idx, g.fd_nxh);
     const int line = l0 + ll;
-    cpx<T> v = {(T)0, (T)0};
-    if (line < nlines) v = spec[(size_t)l0 * nxh + idx];
-    b[idx] = v;
+    if (line < nlines)
+      cp_async<sizeof(cpx<T>)>(&b[idx], &spec[(size_t)l0 * nxh + idx]);
+    else
+      b[idx] = {(T)0, (T)0};
   }
+  cp_async_wait_all();
   __syncthreads();
   // Z_k = E_k + i O_k, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(W^k)/2
   for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
-    const int ll = idx / M, k = idx - ll * M;
+    const int ll = (int)fdiv(idx, g.fd_m), k = idx - ll * M;
     const cpx<T> xk = b[ll * nxh + k];
     const cpx<T> xc = b[ll * nxh + (M - k)];
     const cpx<T> e = {(T)0.5 * (xk.x + xc.x), (T)0.5 * (xk.y - xc.y)};
@@ -217,20 +274,26 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
     a[idx] = {e.x - o.y, e.y + o.x};
   }
   __syncthreads();
-  cpx<T>* z = fft_lines<T, true>(a, b, lpb, rp, M, 1, tw, 2, false);
+  cpx<T>* z = fft_lines<T, true>(a, b, ilog2_dev(lpb), rp, M, 1, tw, 2, false);
+  const df sdf = d2df(scale);
   for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
-    const int ll = idx / M, n = idx - ll * M;
+    const int ll = (int)fdiv(idx, g.fd_m), n = idx - ll * M;
     const int line = l0 + ll;
     if (line >= nlines) continue;
     const cpx<T> v = z[idx];
-    double* out = p + (size_t)line * nx + 2 * n;
-    const double v0 = scale * (double)v.x, v1 = scale * (double)v.y;
-    if (ACCUM) {
-      out[0] += v0;
-      out[1] += v1;
+    const size_t o = (size_t)line * nx + 2 * n;
+    if (MODE == XI_F64) {
+      p[o] = scale * (double)v.x;
+      p[o + 1] = scale * (double)v.y;
     } else {
-      out[0] = v0;
-      out[1] = v1;
+      const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
+      if (MODE == XI_DF) {
+        reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+      } else {
+        const float4 q = reinterpret_cast<const float4*>(pdf)[o >> 1];
+        const df s0 = df_add(df{q.x, q.y}, d0), s1 = df_add(df{q.z, q.w}, d1);
+        reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+      }
     }
   }
 }
@@ -257,36 +320,33 @@ cudaError_t set_smem_limits() {
   cudaError_t e = cudaSuccess;
 #define PPE_SET(K) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  PPE_SET((k_xfwd<T, SRC_RHS, true>));
-  PPE_SET((k_xfwd<T, SRC_RHS, false>));
   PPE_SET((k_xfwd<T, SRC_F, true>));
   PPE_SET((k_xfwd<T, SRC_RESID, true>));
   PPE_SET((k_xfwd<T, SRC_RESID, false>));
   PPE_SET((k_zfft<T, false>));
   PPE_SET((k_zfft<T, true>));
-  PPE_SET((k_xinv<T, false>));
-  PPE_SET((k_xinv<T, true>));
+  PPE_SET((k_ythomas<T>));
+  PPE_SET((k_xinv<T, XI_F64>));
+  PPE_SET((k_xinv<T, XI_DF>));
+  PPE_SET((k_xinv<T, XI_DF_ACC>));
 #undef PPE_SET
+  if (e == cudaSuccess) e = set_rhs_smem_limit<T>();
   return e;
 }
 
 template <typename T>
 cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn& in, DevScalars* sc, int slot,
-                        double* f_out, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, int lpb,
+                        df* fdf, const df* pdf, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, int lpb,
                         cudaStream_t st) {
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
   const size_t sm = do_fft ? xfwd_smem<T>(g.nx, lpb) : sizeof(T) * (size_t)lpb * g.nx;
-  if (src == SRC_RHS && do_fft)
-    k_xfwd<T, SRC_RHS, true><<<grid, 256, sm, st>>>(g, in, sc, slot, f_out, spec, rp, tw, lpb);
-  else if (src == SRC_RHS)
-    k_xfwd<T, SRC_RHS, false><<<grid, 256, sm, st>>>(g, in, sc, slot, f_out, spec, rp, tw, lpb);
-  else if (src == SRC_F)
-    k_xfwd<T, SRC_F, true><<<grid, 256, sm, st>>>(g, in, sc, slot, f_out, spec, rp, tw, lpb);
+  if (src == SRC_F)
+    k_xfwd<T, SRC_F, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
   else if (do_fft)
-    k_xfwd<T, SRC_RESID, true><<<grid, 256, sm, st>>>(g, in, sc, slot, f_out, spec, rp, tw, lpb);
+    k_xfwd<T, SRC_RESID, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
   else
-    k_xfwd<T, SRC_RESID, false><<<grid, 256, sm, st>>>(g, in, sc, slot, f_out, spec, rp, tw, lpb);
+    k_xfwd<T, SRC_RESID, false><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
   return cudaGetLastError();
 }
 
@@ -304,23 +364,40 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
 }
 
 template <typename T>
+size_t ythomas_smem(int ny, int tl) {
+  return sizeof(cpx<T>) * (size_t)ny * tl + sizeof(T) * (size_t)tl * (ny + 1);
+}
+
+// kx lines per CTA: 256-byte rows of the tile when it fits, fewer for tall ny
+template <typename T>
+int ythomas_lines(int ny) {
+  int tl = 256 / (int)sizeof(cpx<T>);
+  while (tl > 1 && ythomas_smem<T>(ny, tl) > 100 * 1024) tl /= 2;
+  return tl;
+}
+
+template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* off, const int* len, T a,
                            const DevScalars* sc, cudaStream_t st) {
-  const int lines = (g.nx / 2 + 1) * g.nz;
-  k_ythomas<T><<<(lines + 127) / 128, 128, 0, st>>>(g, spec, tab, off, len, a, sc);
+  const int nxh = g.nx / 2 + 1;
+  const int tl = ythomas_lines<T>(g.ny);
+  const int grid = g.nz * ((nxh + tl - 1) / tl);
+  k_ythomas<T><<<grid, 128, ythomas_smem<T>(g.ny, tl), st>>>(g, spec, tab, off, len, a, tl, sc);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_xinv(bool accumulate, const GridDev& g, const cpx<T>* spec, double* p, double scale,
+cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp, const cpx<T>* tw, int lpb, const DevScalars* sc, cudaStream_t st) {
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
   const size_t sm = xinv_smem<T>(g.nx, lpb);
-  if (accumulate)
-    k_xinv<T, true><<<grid, 256, sm, st>>>(g, spec, p, scale, rp, tw, lpb, sc);
+  if (mode == XI_F64)
+    k_xinv<T, XI_F64><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+  else if (mode == XI_DF)
+    k_xinv<T, XI_DF><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
   else
-    k_xinv<T, false><<<grid, 256, sm, st>>>(g, spec, p, scale, rp, tw, lpb, sc);
+    k_xinv<T, XI_DF_ACC><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
   return cudaGetLastError();
 }
 
@@ -329,14 +406,14 @@ cudaError_t launch_xinv(bool accumulate, const GridDev& g, const cpx<T>* spec, d
   template size_t zfft_smem<T>(int, int);                                                                        \
   template size_t xinv_smem<T>(int, int);                                                                        \
   template cudaError_t set_smem_limits<T>();                                                                     \
-  template cudaError_t launch_xfwd<T>(int, bool, const GridDev&, const StencilIn&, DevScalars*, int, double*,    \
-                                      cpx<T>*, const RadixPlan&, const cpx<T>*, int, cudaStream_t);             \
+  template cudaError_t launch_xfwd<T>(int, bool, const GridDev&, const StencilIn&, DevScalars*, int, df*,       \
+                                      const df*, cpx<T>*, const RadixPlan&, const cpx<T>*, int, cudaStream_t);  \
   template cudaError_t launch_zfft<T>(bool, const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, int,      \
                                       const DevScalars*, cudaStream_t);                                          \
   template cudaError_t launch_ythomas<T>(const GridDev&, cpx<T>*, const T*, const int*, const int*, T,          \
                                          const DevScalars*, cudaStream_t);                                       \
-  template cudaError_t launch_xinv<T>(bool, const GridDev&, const cpx<T>*, double*, double, const RadixPlan&,   \
-                                      const cpx<T>*, int, const DevScalars*, cudaStream_t);
+  template cudaError_t launch_xinv<T>(int, const GridDev&, const cpx<T>*, double*, df*, double,                  \
+                                      const RadixPlan&, const cpx<T>*, int, const DevScalars*, cudaStream_t);
 PPE_INST(double)
 PPE_INST(float)
 #undef PPE_INST

@@ -32,8 +32,15 @@ struct ppe_plan_s {
   int* line_off;
   int* line_len;
   double a_y;         // 1/dy^2
-  double* fbuf;       // FP64 right-hand side kept for the residual (FP32_REFINE)
+  int tj, kc;         // right-hand-side kernel: lines per tile, planes per chunk
+  df* fdf;            // FP32_REFINE: right-hand side as pairs, kept for the residual
+  df* pdf;            // FP32_REFINE: pressure as pairs during the refinement
+  df* upre;           // explicitly split velocity u_pre on x faces (ppe_project)
+  df* vpre;           //   ... on y faces
+  df* wpre;           //   ... on z faces
   DevScalars* sc;
+  // refinement loop as a CUDA graph with a WHILE conditional node (FP32_REFINE)
+  cudaGraphExec_t refine_exec;
   // ppe_project_host staging (allocated on first use)
   double* io[12];
   size_t workspace;
@@ -64,6 +71,11 @@ RadixPlan radix_plan(int n) {
   while (m % 4 == 0) { rp.r[rp.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { rp.r[rp.nst++] = 2; m /= 2; }
   while (m % 3 == 0) { rp.r[rp.nst++] = 3; m /= 3; }
+  int ns = 1;
+  for (int s = 0; s < rp.nst; ++s) {
+    rp.ns[s] = make_fastdiv((uint32_t)ns);
+    ns *= rp.r[s];
+  }
   return rp;
 }
 
@@ -172,10 +184,10 @@ ppe_status make_thomas(ppe_plan_t P) {
   return PPE_OK;
 }
 
+// lines per CTA of the x passes: the largest power of two <= 2048/nx, in [1, 64]
 int choose_lpb(int nx) {
-  int l = 2048 / nx;
-  if (l < 1) l = 1;
-  if (l > 64) l = 64;
+  int l = 1;
+  while (2 * l <= 2048 / nx && 2 * l <= 64) l *= 2;
   return l;
 }
 
@@ -189,11 +201,12 @@ int choose_tkx(int nz, bool fp32) {
 ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_ERR_CUDA; }
 
 // Kernel names reported by ppe_profile_read.
-enum KernelId { K_INIT, K_RHO_MIN, K_XFWD_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
-                K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_COUNT };
-const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_xfwd_rhs", "k_xfwd_f",
+enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
+                K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
                                            "k_xfwd_resid", "k_zfft_fwd", "k_ythomas", "k_zfft_inv",
-                                           "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check"};
+                                           "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
+                                           "k_df_to_d"};
 constexpr int kProfMax = 16384;
 
 int prof_begin(ppe_plan_t P, int id) {
@@ -250,40 +263,130 @@ StencilIn make_in(ppe_plan_t P, const double* u, const double* v, const double* 
   return in;
 }
 
-// z forward, y solve, z inverse, x inverse (store or accumulate into p)
+// z forward, y solve, z inverse, x inverse (mode XI_F64: p64 = x; XI_DF:
+// pdf = x; XI_DF_ACC: pdf += x)
 template <typename T>
-ppe_status solve_tail(ppe_plan_t P, double* p, bool accumulate, bool guarded) {
+ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded) {
   const DevScalars* sc = guarded ? P->sc : nullptr;
   cpx<T>* spec = (cpx<T>*)P->spec;
   const double scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
   PPE_LAUNCH(P, K_ZFFT_FWD, launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
-  PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y, sc, P->stream));
+  PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y, sc,
+                                             P->stream));
   PPE_LAUNCH(P, K_ZFFT_INV, launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
-  PPE_LAUNCH(P, accumulate ? K_XINV_ACC : K_XINV, launch_xinv<T>(accumulate, P->gd, spec, p, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
-                         P->stream));
+  PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
+             launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
+                            P->stream));
   return PPE_OK;
 }
 
-// The refinement loop of PPE_FP32_REFINE once p holds the first FP32 solve:
-// r = f - L p (FP64), delta = L^{-1} r (FP32), p += delta, on the device.
-ppe_status refine(ppe_plan_t P, const double* f, double* p) {
+// One refinement step of PPE_FP32_REFINE: residual r_s = f - L p (pairs) into
+// slot sc->iter, then the convergence test.
+ppe_status refine_probe(ppe_plan_t P, cudaGraphConditionalHandle h, int use_handle) {
   StencilIn in;
   memset(&in, 0, sizeof(in));
-  in.f = f;
-  in.p = p;
-  const int smax = P->opt.max_sweeps;
-  cpx<float>* spec = (cpx<float>*)P->spec;
-  for (int s = 1; s <= smax; ++s) {
-    PPE_LAUNCH(P, K_XFWD_RESID, launch_xfwd<float>(SRC_RESID, true, P->gd, in, P->sc, s, nullptr, spec, P->rp_half,
-                               (const cpx<float>*)P->tw_x, P->lpb, P->stream));
-    PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, s, smax, P->stream));
-    ppe_status st = solve_tail<float>(P, p, true, true);
-    if (st != PPE_OK) return st;
-  }
-  PPE_LAUNCH(P, K_XFWD_RESID, launch_xfwd<float>(SRC_RESID, false, P->gd, in, P->sc, smax + 1, nullptr, spec, P->rp_half,
-                             (const cpx<float>*)P->tw_x, P->lpb, P->stream));
-  PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, smax + 1, smax, P->stream));
+  PPE_LAUNCH(P, K_XFWD_RESID, launch_xfwd<float>(SRC_RESID, true, P->gd, in, P->sc, -1, P->fdf, P->pdf,
+                                                 (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x,
+                                                 P->lpb, P->stream));
+  PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, h, use_handle, P->stream));
   return PPE_OK;
+}
+
+// Builds the refinement graph once per plan (it touches plan-owned buffers
+// only):  probe; WHILE(cont) { delta = L^{-1} r (FP32); p += delta; probe }.
+ppe_status build_refine_graph(ppe_plan_t P) {
+  cudaStream_t saved = P->stream;
+  const int saved_prof = P->prof_on;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h;
+  ppe_status st = PPE_OK;
+  auto fail = [&](ppe_status s) {
+    P->stream = saved;
+    P->prof_on = saved_prof;
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    cudaGetLastError();
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  P->stream = cs;
+  P->prof_on = 0;
+  if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(PPE_ERR_CUDA);
+  st = refine_probe(P, h, 1);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t cg = nullptr;
+  if (st == PPE_OK && cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess)
+    st = PPE_ERR_CUDA;
+  cudaGraphNode_t cond = nullptr;
+  cudaGraph_t body = nullptr;
+  if (st == PPE_OK) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&cond, cg, deps, nullptr, ndeps, &cp) != cudaSuccess) st = PPE_ERR_CUDA;
+    else body = cp.conditional.phGraph_out[0];
+  }
+  if (st == PPE_OK &&
+      cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    st = PPE_ERR_CUDA;
+  cudaGraph_t outg = nullptr;
+  if (cudaStreamEndCapture(cs, &outg) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+  if (st != PPE_OK) return fail(st);
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(PPE_ERR_CUDA);
+  st = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false);
+  if (st == PPE_OK) st = refine_probe(P, h, 1);
+  cudaGraph_t outb = nullptr;
+  if (cudaStreamEndCapture(cs, &outb) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+  if (st != PPE_OK) return fail(st);
+  if (cudaGraphInstantiate(&P->refine_exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  P->stream = saved;
+  P->prof_on = saved_prof;
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  return PPE_OK;
+}
+
+// The refinement loop once pdf holds the first FP32 solve.  Normally one graph
+// launch (the loop runs on the device); while per-kernel profiling is on, the
+// same kernels are launched from the host, reading the test result after each
+// check so that no empty sweep is launched.
+ppe_status refine(ppe_plan_t P) {
+  if (!P->prof_on) {
+    PPE_TRY(cudaGraphLaunch(P->refine_exec, P->stream));
+    return PPE_OK;
+  }
+  cudaGraphConditionalHandle none = 0;
+  ppe_status s = refine_probe(P, none, 0);
+  while (s == PPE_OK) {
+    int cont = 0;
+    PPE_TRY(cudaMemcpyAsync(&cont, &P->sc->cont, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    PPE_TRY(cudaStreamSynchronize(P->stream));
+    if (!cont) break;
+    if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) break;
+    s = refine_probe(P, none, 0);
+  }
+  return s;
+}
+
+// Tile sizes of the right-hand-side kernel: largest tj in {8, 4, 2, 1} whose
+// shared memory lets two CTAs share an SM, else one.
+void choose_rhs_tiles(ppe_plan_t P) {
+  const int nx = P->g.nx;
+  auto sm = [&](int tj) { return P->fp32 ? rhs_smem<float>(nx, tj) : rhs_smem<double>(nx, tj); };
+  int tj = 4;
+  while (tj > 1 && sm(tj) > 110 * 1024) tj /= 2;
+  if (sm(tj) > 110 * 1024) tj = 1;
+  P->tj = tj;
+  P->kc = P->g.nz < 16 ? P->g.nz : 16;
 }
 
 }  // namespace
@@ -315,7 +418,8 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   const size_t n = (size_t)g->nx * g->ny * g->nz;
   const size_t nxh = g->nx / 2 + 1;
   size_t b = cb * nxh * g->ny * g->nz + cb * (g->nx + g->nz) + sizeof(DevScalars);
-  if (fp32) b += 8 * n;
+  if (fp32) b += 16 * n;                                                 // f, p as pairs
+  b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
   return b;
 }
@@ -358,6 +462,11 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->gd.idx = g->nx / g->lx;
   P->gd.idy = g->ny / g->ly;
   P->gd.idz = g->nz / g->lz;
+  P->gd.fd_nx = make_fastdiv((uint32_t)g->nx);
+  P->gd.fd_nxh = make_fastdiv((uint32_t)(g->nx / 2 + 1));
+  P->gd.fd_m = make_fastdiv((uint32_t)(g->nx / 2));
+  P->gd.fd_ny = make_fastdiv((uint32_t)g->ny);
+  P->gd.fd_nyp1 = make_fastdiv((uint32_t)(g->ny + 1));
   const double dy = g->ly / g->ny;
   P->a_y = 1.0 / (dy * dy);
   P->rp_half = radix_plan(g->nx / 2);
@@ -370,10 +479,15 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   const size_t nspec = (size_t)P->nxh * g->ny * g->nz;
   s = alloc_status(cudaMalloc(&P->spec, nspec * P->cplx_bytes));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->sc, sizeof(DevScalars)));
-  if (s == PPE_OK && P->fp32)
-    s = alloc_status(cudaMalloc((void**)&P->fbuf, sizeof(double) * (size_t)g->nx * g->ny * g->nz));
-  P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 8 * (size_t)g->nx * g->ny * g->nz : 0) +
-                 P->cplx_bytes * (g->nx + g->nz);
+  const size_t ncell = (size_t)g->nx * g->ny * g->nz, nvf = (size_t)g->nx * (g->ny + 1) * g->nz;
+  if (s == PPE_OK && P->fp32) s = alloc_status(cudaMalloc((void**)&P->fdf, sizeof(df) * ncell));
+  if (s == PPE_OK && P->fp32) s = alloc_status(cudaMalloc((void**)&P->pdf, sizeof(df) * ncell));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
+  P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 * sizeof(df) * ncell : 0) +
+                 sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz);
+  choose_rhs_tiles(P);
   if (s == PPE_OK) {
     if (P->fp32) {
       s = make_twiddles<float>(&P->tw_x, g->nx);
@@ -387,7 +501,10 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       if (s == PPE_OK) s = cuda_status(set_smem_limits<double>());
     }
   }
-  if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, -1.0, o.refine_tol, 0, P->stream));
+  if (s == PPE_OK && P->fp32) s = build_refine_graph(P);
+  if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, 1.0, o.refine_tol, 0, P->stream));
+  // grid-only constants (1/dx^2 ...) for a ppe_solve that no ppe_rhs preceded
+  if (s == PPE_OK) s = cuda_status(launch_make_const(P->gd, P->sc, 1.0, P->stream));
   if (s == PPE_OK) s = cuda_status(cudaStreamSynchronize(P->stream));
   if (s != PPE_OK) {
     ppe_destroy(P);
@@ -411,8 +528,13 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->tab);
   cudaFree(P->line_off);
   cudaFree(P->line_len);
-  cudaFree(P->fbuf);
+  cudaFree(P->fdf);
+  cudaFree(P->pdf);
+  cudaFree(P->upre);
+  cudaFree(P->vpre);
+  cudaFree(P->wpre);
   cudaFree(P->sc);
+  if (P->refine_exec) cudaGraphExecDestroy(P->refine_exec);
   for (int i = 0; i < 12; ++i) cudaFree(P->io[i]);
   if (P->prof_ev)
     for (cudaEvent_t e : *P->prof_ev) cudaEventDestroy(e);
@@ -460,12 +582,13 @@ ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double*
   const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
   PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, rho0, P->opt.refine_tol, 0, P->stream));
   if (!(rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(rho, n, P->sc, P->stream));
+  PPE_TRY(launch_make_const(P->gd, P->sc, dt, P->stream));
   if (P->fp32)
-    PPE_LAUNCH(P, K_XFWD_RHS, launch_xfwd<float>(SRC_RHS, false, P->gd, in, P->sc, 0, f, nullptr, P->rp_half, nullptr, P->lpb,
-                               P->stream));
+    PPE_LAUNCH(P, K_RHS, launch_rhs<float>(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                           P->rp_half, (const cpx<float>*)P->tw_x, P->tj, P->kc, P->stream));
   else
-    PPE_LAUNCH(P, K_XFWD_RHS, launch_xfwd<double>(SRC_RHS, false, P->gd, in, P->sc, 0, f, nullptr, P->rp_half, nullptr, P->lpb,
-                                P->stream));
+    PPE_LAUNCH(P, K_RHS, launch_rhs<double>(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                            P->rp_half, (const cpx<double>*)P->tw_x, P->tj, P->kc, P->stream));
   return PPE_OK;
 }
 
@@ -475,16 +598,21 @@ ppe_status ppe_solve(ppe_plan_t P, const double* f, double* p) {
   memset(&in, 0, sizeof(in));
   in.f = f;
   PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, -1.0, P->opt.refine_tol, 1, P->stream));
+  ppe_status s;
   if (P->fp32) {
-    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_F, true, P->gd, in, P->sc, 0, nullptr, (cpx<float>*)P->spec, P->rp_half,
-                               (const cpx<float>*)P->tw_x, P->lpb, P->stream));
-    ppe_status s = solve_tail<float>(P, p, false, false);
-    if (s != PPE_OK) return s;
-    return refine(P, f, p);
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_F, true, P->gd, in, P->sc, 0, P->fdf, nullptr,
+                                               (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->lpb,
+                                               P->stream));
+    if ((s = solve_tail<float>(P, XI_DF, nullptr, P->pdf, false)) != PPE_OK) return s;
+    if ((s = refine(P)) != PPE_OK) return s;
+    PPE_LAUNCH(P, K_DF_TO_D,
+               launch_df_to_d(P->pdf, p, (size_t)P->g.nx * P->g.ny * P->g.nz, P->stream));
+    return PPE_OK;
   }
-  PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_F, true, P->gd, in, P->sc, 0, nullptr, (cpx<double>*)P->spec, P->rp_half,
-                              (const cpx<double>*)P->tw_x, P->lpb, P->stream));
-  return solve_tail<double>(P, p, false, false);
+  PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_F, true, P->gd, in, P->sc, 0, nullptr, nullptr,
+                                              (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->lpb,
+                                              P->stream));
+  return solve_tail<double>(P, XI_F64, p, nullptr, false);
 }
 
 ppe_status ppe_correct(ppe_plan_t P, const double* u, const double* v, const double* w, const double* rho,
@@ -495,7 +623,8 @@ ppe_status ppe_correct(ppe_plan_t P, const double* u, const double* v, const dou
   StencilIn in = make_in(P, u, v, w, nullptr, rho, p_n, p_nm1, dt);
   in.p = p;
   if (rho0 > 0) PPE_TRY(launch_set_rho0(P->sc, rho0, P->stream));
-  PPE_LAUNCH(P, K_CORRECT, launch_correct(P->gd, in, P->sc, u_out, v_out, w_out, P->stream));
+  PPE_TRY(launch_make_const(P->gd, P->sc, dt, P->stream));
+  PPE_LAUNCH(P, K_CORRECT, launch_correct_full(P->gd, in, P->sc, u_out, v_out, w_out, P->stream));
   return PPE_OK;
 }
 
@@ -507,20 +636,24 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
   const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
   PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, F->rho0, P->opt.refine_tol, 0, P->stream));
   if (!(F->rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(F->rho, n, P->sc, P->stream));
+  PPE_TRY(launch_make_const(P->gd, P->sc, F->dt, P->stream));
   ppe_status s;
   if (P->fp32) {
-    double* f = F->f ? F->f : P->fbuf;
-    PPE_LAUNCH(P, K_XFWD_RHS, launch_xfwd<float>(SRC_RHS, true, P->gd, in, P->sc, 0, f, (cpx<float>*)P->spec, P->rp_half,
-                               (const cpx<float>*)P->tw_x, P->lpb, P->stream));
-    if ((s = solve_tail<float>(P, F->p, false, false)) != PPE_OK) return s;
-    if ((s = refine(P, f, F->p)) != PPE_OK) return s;
+    PPE_LAUNCH(P, K_RHS, launch_rhs<float>(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre,
+                                           (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->tj,
+                                           P->kc, P->stream));
+    if ((s = solve_tail<float>(P, XI_DF, nullptr, P->pdf, false)) != PPE_OK) return s;
+    if ((s = refine(P)) != PPE_OK) return s;
+    PPE_LAUNCH(P, K_CORRECT, launch_correct_pre(P->gd, F->dt, P->upre, P->vpre, P->wpre, P->pdf, F->p, P->sc,
+                                                F->u_out, F->v_out, F->w_out, P->stream));
   } else {
-    PPE_LAUNCH(P, K_XFWD_RHS, launch_xfwd<double>(SRC_RHS, true, P->gd, in, P->sc, 0, F->f, (cpx<double>*)P->spec, P->rp_half,
-                                (const cpx<double>*)P->tw_x, P->lpb, P->stream));
-    if ((s = solve_tail<double>(P, F->p, false, false)) != PPE_OK) return s;
+    PPE_LAUNCH(P, K_RHS, launch_rhs<double>(P->gd, in, P->sc, F->f, nullptr, P->upre, P->vpre, P->wpre,
+                                            (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->tj,
+                                            P->kc, P->stream));
+    if ((s = solve_tail<double>(P, XI_F64, F->p, nullptr, false)) != PPE_OK) return s;
+    PPE_LAUNCH(P, K_CORRECT, launch_correct_pre(P->gd, F->dt, P->upre, P->vpre, P->wpre, nullptr, F->p, P->sc,
+                                                F->u_out, F->v_out, F->w_out, P->stream));
   }
-  in.p = F->p;
-  PPE_LAUNCH(P, K_CORRECT, launch_correct(P->gd, in, P->sc, F->u_out, F->v_out, F->w_out, P->stream));
   return PPE_OK;
 }
 

@@ -4,12 +4,25 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "fft.cuh"
 
 namespace ppe {
 
 constexpr int kMaxSweeps = 16;
 constexpr int kMaxDim = 1024;
+
+// Per-call constants of the stencils as float pairs, formed once on the device
+// (k_make_const) after rho_0 is known, and read by every stencil thread.
+struct StencilConst {
+  df c;            // rho_0 / dt
+  df g;            // dt / rho_0
+  df r0h;          // rho_0 / 2   (harmonic face rule)
+  df r02;          // 2 rho_0     (arithmetic face rule)
+  df idx, idy, idz;
+  df gx, gy, gz;   // (dt/rho_0) / dx, ...
+  df lx, ly, lz;   // 1/dx^2, 1/dy^2, 1/dz^2
+};
 
 // Device-resident scalars of one plan.  Non-negative doubles are kept as their
 // IEEE bit patterns so that atomicMax / atomicMin on unsigned 64-bit integers
@@ -19,15 +32,25 @@ struct DevScalars {
   unsigned long long fmax_bits;                 // ||f||_inf
   unsigned long long rmax_bits[kMaxSweeps + 2]; // ||f - L p||_inf measured before sweep s
   int done;                                     // refinement converged
+  int iter;                                     // residual slot of the next check (1-based)
+  int cont;                                     // last check asked for another correction
   int last_slot;                                // slot of the last residual checked (-1: none)
   int sweeps;                                   // sweeps run
   double tol;                                   // refinement tolerance (relative)
+  StencilConst K;                               // stencil constants of the current call
 };
 
 struct GridDev {
   int nx, ny, nz;
   double idx, idy, idz;  // 1/dx, 1/dy, 1/dz
+  FastDiv fd_nx, fd_nxh, fd_m, fd_ny, fd_nyp1;  // dividers by nx, nx/2+1, nx/2, ny, ny+1
 };
+
+inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << (l + 1)) <= v) ++l;
+  return l;
+}
 
 // Inputs of the right-hand side (Eq. (34)) and of the correction (Eq. (33)).
 struct StencilIn {
@@ -39,12 +62,23 @@ struct StencilIn {
   int face_rule;     // 0 arithmetic, 1 harmonic
 };
 
-enum XSource { SRC_RHS = 0, SRC_F = 1, SRC_RESID = 2 };
+enum XSource { SRC_F = 1, SRC_RESID = 2 };
+enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
+
+// ---- launchers (k_rhs.cu) ----
+template <typename T>
+cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
+                       df* vpre, df* wpre, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, int tj, int kc,
+                       cudaStream_t st);
+template <typename T>
+size_t rhs_smem(int nx, int tj);
+template <typename T>
+cudaError_t set_rhs_smem_limit();
 
 // ---- launchers (k_spectral.cu) ----
 template <typename T>
 cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn& in, DevScalars* sc,
-                        int sweep_slot, double* f_out, cpx<T>* spec, const RadixPlan& rp_half,
+                        int sweep_slot, df* fdf, const df* pdf, cpx<T>* spec, const RadixPlan& rp_half,
                         const cpx<T>* tw_x, int lpb, cudaStream_t st);
 template <typename T>
 cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const RadixPlan& rp,
@@ -53,7 +87,7 @@ template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* line_off,
                            const int* line_len, T a, const DevScalars* sc, cudaStream_t st);
 template <typename T>
-cudaError_t launch_xinv(bool accumulate, const GridDev& g, const cpx<T>* spec, double* p, double scale,
+cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp_half, const cpx<T>* tw_x, int lpb, const DevScalars* sc,
                         cudaStream_t st);
 template <typename T>
@@ -68,9 +102,21 @@ cudaError_t set_smem_limits();
 // ---- launchers (k_stencil.cu) ----
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st);
 cudaError_t launch_set_rho0(DevScalars* sc, double rho0, cudaStream_t st);
+// Forms sc->K from sc->rho0, dt and the grid (one thread).
+cudaError_t launch_make_const(const GridDev& g, DevScalars* sc, double dt, cudaStream_t st);
 cudaError_t launch_rho_min(const double* rho, size_t n, DevScalars* sc, cudaStream_t st);
-cudaError_t launch_correct(const GridDev& g, const StencilIn& in, const DevScalars* sc, double* u_out,
-                           double* v_out, double* w_out, cudaStream_t st);
-cudaError_t launch_refine_check(DevScalars* sc, int sweep, int smax, cudaStream_t st);
+// u^{n+1} = u_pre - (dt/rho_0) G p with p as pairs (pdf) or FP64 (p64); also
+// writes p64 from pdf when both are given.
+cudaError_t launch_correct_pre(const GridDev& g, double dt, const df* upre, const df* vpre, const df* wpre,
+                               const df* pdf, double* p64, const DevScalars* sc, double* u_out, double* v_out,
+                               double* w_out, cudaStream_t st);
+// Eq. (33) from the raw inputs (the separate ppe_correct entry point).
+cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const DevScalars* sc, double* u_out,
+                                double* v_out, double* w_out, cudaStream_t st);
+cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st);
+// Convergence test of the residual in slot sc->iter; sets sc->cont and, when
+// use_handle, the WHILE condition of the refinement graph.
+cudaError_t launch_refine_check(DevScalars* sc, int smax, cudaGraphConditionalHandle handle, int use_handle,
+                                cudaStream_t st);
 
 }  // namespace ppe

@@ -1,0 +1,51 @@
+// Host harness for paper_2103_01874_gb300/csrc/dfloat.cuh and fastdiv.cuh:
+// reads commands on stdin, prints results (floats as C99 hex).  Built and
+// driven by test_dfloat.py.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "dfloat.cuh"
+#include "fastdiv.cuh"
+
+using namespace ppe;
+
+int main() {
+  char op[16];
+  while (std::scanf("%15s", op) == 1) {
+    if (!std::strcmp(op, "fastdiv")) {
+      // fastdiv d x0 count stride: prints the number of mismatches
+      unsigned d, x0, count, stride;
+      std::scanf("%u %u %u %u", &d, &x0, &count, &stride);
+      const FastDiv f = make_fastdiv(d);
+      unsigned long bad = 0;
+      for (unsigned long c = 0; c < count; ++c) {
+        const unsigned long x = x0 + c * (unsigned long)stride;
+        if (x >= (1ul << 31)) break;
+        if (fdiv((uint32_t)x, f) != (uint32_t)(x / d) || fmod_((uint32_t)x, f) != (uint32_t)(x % d)) ++bad;
+      }
+      std::printf("%lu\n", bad);
+    } else if (!std::strcmp(op, "d2df")) {
+      double x;
+      std::scanf("%la", &x);
+      df r = d2df(x);
+      std::printf("%a %a\n", (double)r.hi, (double)r.lo);
+    } else if (!std::strcmp(op, "df2d")) {
+      double h, l;
+      std::scanf("%la %la", &h, &l);
+      std::printf("%a\n", df2d(df{(float)h, (float)l}));
+    } else {
+      double ah, al, bh, bl;
+      std::scanf("%la %la %la %la", &ah, &al, &bh, &bl);
+      df a{(float)ah, (float)al}, b{(float)bh, (float)bl}, r;
+      if (!std::strcmp(op, "add")) r = df_add(a, b);
+      else if (!std::strcmp(op, "sub")) r = df_sub(a, b);
+      else if (!std::strcmp(op, "mul")) r = df_mul(a, b);
+      else if (!std::strcmp(op, "mulf")) r = df_mul_f(a, b.hi);
+      else if (!std::strcmp(op, "recip")) r = df_recip(a);
+      else return 2;
+      std::printf("%a %a\n", (double)r.hi, (double)r.lo);
+    }
+  }
+  return 0;
+}
