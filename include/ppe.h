@@ -168,6 +168,28 @@ typedef struct {
 ppe_status ppe_profile(ppe_plan_t plan, int enable);
 int ppe_profile_read(ppe_plan_t plan, ppe_kernel_time* out, int max_entries);
 
+/* rho_0 = min(rho) without allocating device memory.  The paper has no
+ * counterpart of this entry point: it serves callers that cannot call
+ * cudaMalloc -- code whose device memory belongs to another owner's budget (a
+ * framework's caching allocator, a serving loop's admission control), where an
+ * extra allocation can fail or overrun the budget, and latency-critical code
+ * for which cudaMalloc may synchronise the device.  It computes the same value
+ * as the reduction ppe_rhs / ppe_project run when rho0 <= 0.
+ *   rho       device, n doubles, all > 0 (densities), not NaN;
+ *   n         1 <= n <= 67,108,864 (16384 blocks of 4096 cells); larger n
+ *             returns PPE_ERR_UNSUPPORTED_SIZE before anything is launched,
+ *             n == 0 or a NULL pointer returns PPE_ERR_INVALID_ARG;
+ *   rho0_out  device pointer to one double, written asynchronously on `stream`
+ *             (a cudaStream_t, NULL = legacy default stream).
+ * Scratch: a static __device__ array of about 128 KiB inside libppe (one copy
+ * on every GPU that loads the library, held until the process exits).  Every
+ * call shares it, so calls that overlap on the GPU race and must be serialised
+ * by the caller; each call clears the part that must start at zero.  The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * No call allocates: no cudaMalloc, cudaFree or allocating library routine. */
+ppe_status ppe_rho0_noalloc(const double* rho, size_t n, double* rho0_out, void* stream);
+
 /* Static text for a status code. */
 const char* ppe_strerror(ppe_status status);
 

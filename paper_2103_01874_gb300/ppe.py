@@ -72,6 +72,7 @@ SIGNATURES = {
     "ppe_strerror": (ctypes.c_char_p, [c_int]),
     "ppe_size_supported": (c_int, [c_int, c_int, c_int]),
     "ppe_profile": (c_int, [c_void_p, c_int]),
+    "ppe_rho0_noalloc": (c_int, [c_void_p, c_size_t, c_void_p, c_void_p]),
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
 }
 
@@ -141,6 +142,25 @@ def _hptr(a, shape, name):
             raise ValueError(f"{name}: need a contiguous float64 CPU tensor of shape {shape}")
         return a.data_ptr()
     raise TypeError(name)
+
+
+RHO0_NOALLOC_MAX = 16384 * 4096
+
+
+def rho0_noalloc(rho, out, stream=None):
+    """ppe_rho0_noalloc: min(rho) into the one-element float64 CUDA tensor
+    `out`, using the library's static scratch instead of any allocation (for
+    callers that cannot allocate device memory).  Asynchronous on `stream`."""
+    import torch
+    if not (isinstance(rho, torch.Tensor) and rho.is_cuda and rho.dtype == torch.float64 and rho.is_contiguous()):
+        raise ValueError("rho: need a contiguous float64 CUDA tensor")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise ValueError("out: need a float64 CUDA tensor with at least one element")
+    if rho.numel() > RHO0_NOALLOC_MAX:
+        raise ValueError(f"rho has {rho.numel()} values; the static scratch of ppe_rho0_noalloc "
+                         f"holds at most {RHO0_NOALLOC_MAX}")
+    _check(lib().ppe_rho0_noalloc(rho.data_ptr(), rho.numel(), out.data_ptr(),
+                                  c_void_p(_stream_handle(stream))), "ppe_rho0_noalloc")
 
 
 def _stream_handle(stream):
