@@ -131,7 +131,7 @@ def kernel_bytes(kernel: str, fp32: bool) -> float:
         "k_xfwd_f": F + spec,
         "k_xfwd_resid": 2 * F + spec,                   # f, p (pairs) -> spectrum
         "k_zfft_fwd": 2 * spec,
-        "k_ythomas": 2 * spec,
+        "k_ysolve": 2 * spec,
         "k_zfft_inv": 2 * spec,
         "k_xinv": spec + F,                             # -> p (FP64 or pairs)
         "k_xinv_accum": spec + 2 * F,                   # p += delta (pairs)

@@ -154,6 +154,23 @@ ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
 /* Free the workspace.  NULL is ignored. */
 void ppe_destroy(ppe_plan_t plan);
 
+/* Launch-shape tuning of a plan (what an autotuner sweeps).  Every field is a
+ * tile size of one pass; results do not depend on them.
+ *   rhs_lines   y-lines per CTA of the right-hand-side kernel: 1, 2, 4 or 8
+ *   rhs_planes  z-planes each of its CTAs marches through: 1 .. nz
+ *   x_lines     x-lines per CTA of the x transforms: power of two in 1 .. 64
+ *   z_cols      kx columns per CTA of the z transforms: 1, 2, 4, 8 or 16
+ *   y_cols      kx columns per CTA of the y pass (FP32_REFINE): 1 .. 32, power of two
+ * ppe_set_tuning returns PPE_ERR_INVALID_ARG (and changes nothing) if a value
+ * is outside its range or a pass would need more than 227 KB of shared memory
+ * per CTA.  Synchronises the plan's stream (captured refinement graphs are
+ * rebuilt with the new shapes). */
+typedef struct {
+    int rhs_lines, rhs_planes, x_lines, z_cols, y_cols;
+} ppe_tuning;
+ppe_status ppe_get_tuning(ppe_plan_t plan, ppe_tuning* out);
+ppe_status ppe_set_tuning(ppe_plan_t plan, const ppe_tuning* tuning);
+
 /* Per-kernel timing.  While enabled, every kernel the plan launches is
  * bracketed by two CUDA events on the plan's stream.  ppe_profile_read
  * synchronises the stream, aggregates the records by kernel into `out`

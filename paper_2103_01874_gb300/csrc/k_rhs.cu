@@ -1,5 +1,4 @@
-// Right-hand side of the split pressure Poisson equation, Eq. (34), fused with
-// the forward real FFT along x.
+// Right-hand side of the split pressure Poisson equation, Eq. (34).
 //
 //   f = D[beta_f G p_hat] + (rho_0/dt)(D u* - S),  beta_f = 1 - rho_0/rho_f,
 //   p_hat = 2 p^n - p^{n-1}                                        (Eq. (32))
@@ -19,9 +18,8 @@
 // above, p_hat and rho of the tj lines plus one halo line on each side (a
 // 2-plane ring), and the face values Q of the x faces, y faces and the two z
 // faces of the current plane.  Each input value is converted once per CTA
-// (plus halo), each face is evaluated once.  After the cells of a plane are
-// formed, the tj x-lines are transformed in shared memory (Stockham, fft.cuh)
-// and the half spectrum is written in the [k][j][kx] layout.
+// (plus halo), each face is evaluated once.  f is written as float pairs (the
+// forward x transform reads it back, k_xfwd) and/or as FP64.
 #include "dfloat.cuh"
 #include "ppe_internal.h"
 #include "stencil.cuh"
@@ -34,16 +32,12 @@ struct RhsOut {
   df* upre;      // optional: u_pre on x faces  [nz][ny][nx]
   df* vpre;      //           v_pre on y faces  [nz][ny+1][nx]
   df* wpre;      //           w_pre on z faces  [nz][ny][nx]
-  void* spec;    // optional: half spectrum (cpx<T>)
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out,
-                                                   RadixPlan rp, const cpx<T>* __restrict__ tw, int tj, int kc,
-                                                   int do_fft) {
+__global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int tj,
+                                                   int kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int M = nx / 2, nxh = M + 1;
   const int ntile = (ny + tj - 1) / tj;
   const int jt = blockIdx.x % ntile, kci = blockIdx.x / ntile;
   const int j0 = jt * tj, k0 = kci * kc;
@@ -57,8 +51,6 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
   df* QX = R + 2 * nl * nx;                         // [tj][nx]
   df* QY = QX + tj * nx;                            // [tj+1][nx]
   df* QZ = QY + (tj + 1) * nx;                      // [2][tj][nx]
-  T* line_re = reinterpret_cast<T*>(QZ + 2 * tj * nx);  // [tj][nx]
-  cpx<T>* bufb = reinterpret_cast<cpx<T>*>(line_re + tj * nx);  // [tj][M]
 
   const StencilConst K = sc->K;  // formed once per call by k_make_const
   const size_t plane = (size_t)ny * nx;
@@ -238,7 +230,6 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         if (idx >= tj * nx) continue;
         const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
         const int j = j0 + jj;
-        T val = (T)0;
         if (j < ny) {
           const int ip = (i + 1 == nx) ? 0 : i + 1;
           const df dxq = df_mul(df_sub(QX[jj * nx + ip], QX[idx]), K.idx);
@@ -247,36 +238,9 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
           const size_t c = (size_t)k * plane + (size_t)j * nx + i;
           const df f = df_sub(df_add(df_add(dxq, dyq), dzq), df_mul(K.c, d2df(ss_[u])));
           if (out.fdf) out.fdf[c] = f;
-          if (out.f64 || sizeof(T) == 8) {
-            const double fd = df2d(f);
-            if (out.f64) out.f64[c] = fd;
-            val = (sizeof(T) == 8) ? (T)fd : (T)df_to_f(f);
-          } else {
-            val = (T)df_to_f(f);
-          }
+          if (out.f64) out.f64[c] = df2d(f);
           vmax = fmaxf(vmax, fabsf(f.hi));
         }
-        line_re[idx] = val;
-      }
-    }
-    __syncthreads();
-    // ---- forward x transform of the tj lines of plane k
-    if (do_fft) {
-      cpx<T>* z = fft_lines<T, false>(reinterpret_cast<cpx<T>*>(line_re), bufb, __ffs(tj) - 1, rp, M, 1, tw, 2, false);
-      cpx<T>* spec = reinterpret_cast<cpx<T>*>(out.spec);
-      for (int idx = threadIdx.x; idx < tj * nxh; idx += blockDim.x) {
-        const int jj = (int)fdiv(idx, g.fd_nxh), kx = idx - jj * nxh;
-        const int j = j0 + jj;
-        if (j >= ny) continue;
-        const cpx<T> zk = z[jj * M + (kx == M ? 0 : kx)];
-        const cpx<T> zc = z[jj * M + (kx == 0 ? 0 : M - kx)];
-        const cpx<T> aa = {zk.x + zc.x, zk.y - zc.y};
-        const cpx<T> bb = {zk.x - zc.x, zk.y + zc.y};
-        const cpx<T> wb = cmul(tw[kx], bb);
-        cpx<T> X;
-        X.x = (T)0.5 * (aa.x + wb.y);
-        X.y = (T)0.5 * (aa.y - wb.x);
-        spec[((size_t)k * ny + j) * nxh + kx] = X;
       }
     }
     // ---- slot a (plane k) is free: load plane k+2 for the next step
@@ -286,43 +250,27 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
   block_max_to(&sc->fmax_bits, vmax);
 }
 
-template <typename T>
 size_t rhs_smem(int nx, int tj) {
   const size_t nl = tj + 2;
-  return sizeof(df) * (4 * nl * nx + (size_t)tj * nx + (size_t)(tj + 1) * nx + 2 * (size_t)tj * nx) +
-         sizeof(T) * (size_t)tj * nx + sizeof(cpx<T>) * (size_t)tj * (nx / 2);
+  return sizeof(df) * (4 * nl * nx + (size_t)tj * nx + (size_t)(tj + 1) * nx + 2 * (size_t)tj * nx);
 }
 
-template <typename T>
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
-                       df* vpre, df* wpre, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, int tj, int kc,
-                       cudaStream_t st) {
+                       df* vpre, df* wpre, int tj, int kc, cudaStream_t st) {
   RhsOut o;
   o.f64 = f64;
   o.fdf = fdf;
   o.upre = upre;
   o.vpre = vpre;
   o.wpre = wpre;
-  o.spec = spec;
   const int ntile = (g.ny + tj - 1) / tj;
   const int nchunk = (g.nz + kc - 1) / kc;
-  const size_t sm = rhs_smem<T>(g.nx, tj);
-  k_rhs_march<T><<<ntile * nchunk, 256, sm, st>>>(g, in, sc, o, rp, tw, tj, kc, spec != nullptr);
+  k_rhs_march<<<ntile * nchunk, 256, rhs_smem(g.nx, tj), st>>>(g, in, sc, o, tj, kc);
   return cudaGetLastError();
 }
 
-template <typename T>
 cudaError_t set_rhs_smem_limit() {
-  return cudaFuncSetAttribute(k_rhs_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return cudaFuncSetAttribute(k_rhs_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
-
-template size_t rhs_smem<double>(int, int);
-template size_t rhs_smem<float>(int, int);
-template cudaError_t launch_rhs<double>(const GridDev&, const StencilIn&, DevScalars*, double*, df*, df*, df*, df*,
-                                        cpx<double>*, const RadixPlan&, const cpx<double>*, int, int, cudaStream_t);
-template cudaError_t launch_rhs<float>(const GridDev&, const StencilIn&, DevScalars*, double*, df*, df*, df*, df*,
-                                       cpx<float>*, const RadixPlan&, const cpx<float>*, int, int, cudaStream_t);
-template cudaError_t set_rhs_smem_limit<double>();
-template cudaError_t set_rhs_smem_limit<float>();
 
 }  // namespace ppe

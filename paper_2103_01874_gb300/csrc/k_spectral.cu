@@ -53,13 +53,13 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
     lc[2] = sc->K.lz;
   }
   float vmax = 0.0f;
-  for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
-    const int ll = (int)fdiv(idx, g.fd_nx), i = idx - ll * nx;
-    const int line = l0 + ll;
-    T val = (T)0;
-    if (line < nlines) {
-      const size_t c = (size_t)line * nx + i;
-      if (SRC == SRC_F) {
+  if (SRC == SRC_F) {
+    for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
+      const int ll = (int)fdiv(idx, g.fd_nx);
+      const int line = l0 + ll;
+      T val = (T)0;
+      if (line < nlines) {
+        const size_t c = (size_t)l0 * nx + idx;
         const double x = __ldg(in.f + c);
         if (sizeof(T) == 8) {
           val = (T)x;
@@ -69,17 +69,68 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
           val = (T)df_to_f(v);
         }
         vmax = fmaxf(vmax, fabsf(d2df(x).hi));
-      } else {
-        const int k = (int)fdiv(line, g.fd_ny), j = line - k * g.ny;
-        const df r = resid_df(g, fdf, pdf, lc, i, j, k);
-        val = (T)df_to_f(r);
-        vmax = fmaxf(vmax, fabsf(r.hi));
+      }
+      line_re[idx] = val;
+    }
+  } else if (SRC == SRC_FDF) {
+    // f as pairs, written by the right-hand-side kernel (which also took ||f||)
+    for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
+      const int ll = (int)fdiv(idx, g.fd_nx);
+      T val = (T)0;
+      if (l0 + ll < nlines) {
+        const df v = fdf[(size_t)l0 * nx + idx];
+        val = (sizeof(T) == 8) ? (T)df2d(v) : (T)df_to_f(v);
+      }
+      line_re[idx] = val;
+    }
+  } else {
+    // residual r = f - L p in pairs; two cells per thread per round with all
+    // their loads issued first
+    constexpr int U = 2;
+    for (int b0 = 0; b0 < lpb * nx; b0 += U * blockDim.x) {
+      df pc[U], pxp[U], pxm[U], pyp[U], pym[U], pzp[U], pzm[U], fv[U];
+      int jj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x + threadIdx.x;
+        const int ll = (int)fdiv(idx, g.fd_nx), i = idx - ll * nx;
+        const int line = l0 + ll;
+        jj[u] = -1;
+        if (idx < lpb * nx && line < nlines) {
+          const int k = (int)fdiv(line, g.fd_ny), j = line - k * g.ny;
+          jj[u] = j;
+          const Nbr n = neighbours(g, i, j, k);
+          pc[u] = pdf[n.c];
+          pxp[u] = pdf[n.xp];
+          pxm[u] = pdf[n.xm];
+          pzp[u] = pdf[n.zp];
+          pzm[u] = pdf[n.zm];
+          pyp[u] = (j + 1 < g.ny) ? pdf[n.c + nx] : pc[u];
+          pym[u] = (j > 0) ? pdf[n.c - nx] : pc[u];
+          fv[u] = fdf[n.c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x + threadIdx.x;
+        if (idx >= lpb * nx) continue;
+        T val = (T)0;
+        if (jj[u] >= 0) {
+          const df p0 = pc[u];
+          const df lx = df_sub(df_sub(pxp[u], p0), df_sub(p0, pxm[u]));
+          const df lz = df_sub(df_sub(pzp[u], p0), df_sub(p0, pzm[u]));
+          const df ly = df_sub(df_sub(pyp[u], p0), df_sub(p0, pym[u]));  // wall sides contribute 0
+          const df lap = df_add(df_add(df_mul(lx, lc[0]), df_mul(ly, lc[1])), df_mul(lz, lc[2]));
+          const df r = df_sub(fv[u], lap);
+          val = (T)df_to_f(r);
+          vmax = fmaxf(vmax, fabsf(r.hi));
+        }
+        line_re[idx] = val;
       }
     }
-    line_re[idx] = val;
   }
   if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
-  else block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
+  else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
   if (!DO_FFT) return;
   __syncthreads();
   cpx<T>* z = fft_lines<T, false>(reinterpret_cast<cpx<T>*>(line_re), bufb, ilog2_dev(lpb), rp, M, 1, tw, 2, false);
@@ -236,6 +287,77 @@ __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const 
   }
 }
 
+// y pass of the FP32 solve: DCT-II along y, divide by the eigenvalues of L,
+// DCT-III back -- the cosine basis diagonalises the Neumann operator, so this
+// equals the tridiagonal solve of k_ythomas but is fully parallel.  The
+// DCT-II of a complex line x is formed from one FFT of the reordered line
+// v[pos(j)] = x_j (pos(j) = j/2 for even j, N-1-(j-1)/2 for odd j; Makhoul
+// 1980): X_k = (w_k V_k + conj(w_k) V_{N-k})/2 with w_k = exp(-i pi k/(2N)),
+// V_N = V_0.  The inverse takes V'_k = conj(w_k)(P_k - i P_{N-k}), P_N = 0,
+// an inverse FFT, and x_j = v'[pos(j)] / N.  Eigenvalue of mode (kx, ky, kz):
+// lam_x[kx] + lam_y[ky] + lam_z[kz]; the zero mode is set to zero.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
+                                              const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
+                                              const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nxh = g.nx / 2 + 1, ny = g.ny;
+  const int ntile = (nxh + tky - 1) / tky;
+  const int kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * tky;
+  cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* b = a + (size_t)tky * ny;
+  const int t2 = ilog2_dev(tky);
+  const size_t base = (size_t)kz * ny * nxh + kx0;
+  for (int idx = threadIdx.x; idx < ny * tky; idx += blockDim.x) {
+    const int j = idx >> t2, c = idx & (tky - 1);
+    const int pj = (j & 1) ? ny - 1 - (j >> 1) : (j >> 1);
+    if (kx0 + c < nxh)
+      cp_async<sizeof(cpx<T>)>(&a[pj * tky + c], &spec[base + (size_t)j * nxh + c]);
+    else
+      a[pj * tky + c] = {(T)0, (T)0};
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  cpx<T>* V = fft_lines<T, false>(a, b, t2, rp, 1, tky, tw, 1, true);
+  const T inv_n = (T)1 / (T)ny;
+  const T lz = lam_z[kz];
+  const int npair = ny / 2 + 1;
+  for (int idx = threadIdx.x; idx < npair * tky; idx += blockDim.x) {
+    const int k = idx >> t2, c = idx & (tky - 1);
+    const int kx = kx0 + c;
+    if (kx >= nxh) continue;
+    const T lxz = lam_x[kx] + lz;
+    if (k == 0) {
+      const T lam = lxz + lam_y[0];
+      const cpx<T> v0 = V[c];
+      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n / lam;  // zero mode pinned
+      V[c] = {v0.x * s, v0.y * s};
+      continue;
+    }
+    const int r = ny - k;
+    const cpx<T> vk = V[k * tky + c], vr = V[r * tky + c];
+    const cpx<T> wk = wq[k], wr = wq[r];
+    const cpx<T> wkc = {wk.x, -wk.y}, wrc = {wr.x, -wr.y};
+    const cpx<T> t1 = cmul(wk, vk), t2c = cmul(wkc, vr);
+    const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
+    const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
+    const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
+    const T sk = inv_n / (lxz + lam_y[k]), sr = inv_n / (lxz + lam_y[r]);
+    const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
+    // V'_k = conj(w_k)(P_k - i P_r), V'_r = conj(w_r)(P_r - i P_k);  -i z = (z.y, -z.x)
+    V[k * tky + c] = cmul(wkc, cpx<T>{pk.x + pr.y, pk.y - pr.x});
+    if (r != k) V[r * tky + c] = cmul(wrc, cpx<T>{pr.x + pk.y, pr.y - pk.x});
+  }
+  __syncthreads();
+  cpx<T>* W = (V == a) ? b : a;
+  cpx<T>* R = fft_lines<T, true>(V, W, t2, rp, 1, tky, tw, 1, true);
+  for (int idx = threadIdx.x; idx < ny * tky; idx += blockDim.x) {
+    const int j = idx >> t2, c = idx & (tky - 1);
+    const int pj = (j & 1) ? ny - 1 - (j >> 1) : (j >> 1);
+    if (kx0 + c < nxh) spec[base + (size_t)j * nxh + c] = R[pj * tky + c];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // inverse x pass
 // ---------------------------------------------------------------------------
@@ -321,16 +443,18 @@ cudaError_t set_smem_limits() {
 #define PPE_SET(K) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
   PPE_SET((k_xfwd<T, SRC_F, true>));
+  PPE_SET((k_xfwd<T, SRC_FDF, true>));
   PPE_SET((k_xfwd<T, SRC_RESID, true>));
   PPE_SET((k_xfwd<T, SRC_RESID, false>));
   PPE_SET((k_zfft<T, false>));
   PPE_SET((k_zfft<T, true>));
   PPE_SET((k_ythomas<T>));
+  PPE_SET((k_ydct<T>));
   PPE_SET((k_xinv<T, XI_F64>));
   PPE_SET((k_xinv<T, XI_DF>));
   PPE_SET((k_xinv<T, XI_DF_ACC>));
 #undef PPE_SET
-  if (e == cudaSuccess) e = set_rhs_smem_limit<T>();
+  if (e == cudaSuccess) e = set_rhs_smem_limit();
   return e;
 }
 
@@ -343,6 +467,8 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
   const size_t sm = do_fft ? xfwd_smem<T>(g.nx, lpb) : sizeof(T) * (size_t)lpb * g.nx;
   if (src == SRC_F)
     k_xfwd<T, SRC_F, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+  else if (src == SRC_FDF)
+    k_xfwd<T, SRC_FDF, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
   else if (do_fft)
     k_xfwd<T, SRC_RESID, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
   else
@@ -387,6 +513,15 @@ cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const i
 }
 
 template <typename T>
+cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, const cpx<T>* wq,
+                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, cudaStream_t st) {
+  const int nxh = g.nx / 2 + 1;
+  const int grid = g.nz * ((nxh + tky - 1) / tky);
+  k_ydct<T><<<grid, 256, zfft_smem<T>(g.ny, tky), st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp, const cpx<T>* tw, int lpb, const DevScalars* sc, cudaStream_t st) {
   const int nlines = g.ny * g.nz;
@@ -412,6 +547,8 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
                                       const DevScalars*, cudaStream_t);                                          \
   template cudaError_t launch_ythomas<T>(const GridDev&, cpx<T>*, const T*, const int*, const int*, T,          \
                                          const DevScalars*, cudaStream_t);                                       \
+  template cudaError_t launch_ydct<T>(const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, const cpx<T>*,     \
+                                      const T*, const T*, const T*, int, cudaStream_t);                          \
   template cudaError_t launch_xinv<T>(int, const GridDev&, const cpx<T>*, double*, df*, double,                  \
                                       const RadixPlan&, const cpx<T>*, int, const DevScalars*, cudaStream_t);
 PPE_INST(double)

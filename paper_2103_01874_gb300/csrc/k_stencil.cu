@@ -22,13 +22,26 @@ __global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep
   sc->tol = tol;
 }
 
+// rho > 0 (densities), so the IEEE bit patterns order like the values and the
+// minimum runs on 64-bit integers (no FP64 instructions); 4 loads in flight.
 __global__ void __launch_bounds__(256) k_rho_min(const double* __restrict__ rho, size_t n, DevScalars* sc) {
-  double m = __longlong_as_double(0x7FF0000000000000ll);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    m = fmin(m, __ldg(rho + i));
-  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-  // rho > 0, so the bit patterns order like the values
-  if ((threadIdx.x & 31) == 0) atomicMin(&sc->rho0_bits, (unsigned long long)__double_as_longlong(m));
+  unsigned long long m = 0x7FF0000000000000ull;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    unsigned long long b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t i = i0 + u * stride;
+      b[u] = (i < n) ? (unsigned long long)__double_as_longlong(__ldg(rho + i)) : 0x7FF0000000000000ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = b[u] < m ? b[u] : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = q < m ? q : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(&sc->rho0_bits, m);
 }
 
 // Eq. (33) after the solve, from the explicitly split velocity u_pre written by
@@ -40,26 +53,54 @@ __global__ void __launch_bounds__(256) k_correct_pre(GridDev g, double dt, const
                                                      const df* __restrict__ vpre, const df* __restrict__ wpre,
                                                      const df* __restrict__ pdf, double* p64, const DevScalars* sc,
                                                      double* u_out, double* v_out, double* w_out) {
-  const size_t nx = (size_t)g.nx, ny = (size_t)g.ny;
-  const size_t total = (size_t)g.nz * (ny + 1) * nx;
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+  const uint32_t total = (uint32_t)g.nz * (ny + 1) * nx;
   const StencilConst K = sc->K;
   auto P = [&](size_t c) -> df { return pdf ? pdf[c] : d2df(p64[c]); };
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t r = fdiv((uint32_t)t, g.fd_nx);
-    const int i = (int)((uint32_t)t - r * (uint32_t)nx);
-    const int k = (int)fdiv(r, g.fd_nyp1);
-    const int j = (int)(r - (uint32_t)k * (uint32_t)(ny + 1));
-    const size_t cv = t;  // v index (k*(ny+1) + j)*nx + i
-    if (j == 0 || j == g.ny) {
-      v_out[cv] = df2d(vpre[cv]);
-      if (j == g.ny) continue;
+  constexpr int U = 2;  // faces per thread per round, loads issued first
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
+    df vp[U], up[U], wp[U], p0[U], pym[U], pxm[U], pzm[U];
+    size_t cc[U];
+    int jj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t t = t0 + u * stride;
+      jj[u] = -1;
+      if (t >= total) continue;
+      const uint32_t r = fdiv(t, g.fd_nx);
+      const int i = (int)(t - r * nx);
+      const int k = (int)fdiv(r, g.fd_nyp1);
+      const int j = (int)(r - (uint32_t)k * (ny + 1));
+      jj[u] = j;
+      vp[u] = vpre[t];
+      if (j < (int)ny) {
+        const Nbr n = neighbours(g, i, j, k);
+        cc[u] = n.c;
+        up[u] = upre[n.c];
+        wp[u] = wpre[n.c];
+        p0[u] = P(n.c);
+        pxm[u] = P(n.xm);
+        pzm[u] = P(n.zm);
+        pym[u] = (j > 0) ? P(n.c - nx) : p0[u];
+      }
     }
-    const Nbr n = neighbours(g, i, j, k);
-    const df p0 = P(n.c);
-    if (j > 0) v_out[cv] = df2d(df_sub(vpre[cv], df_mul(K.gy, df_sub(p0, P(n.c - nx)))));
-    u_out[n.c] = df2d(df_sub(upre[n.c], df_mul(K.gx, df_sub(p0, P(n.xm)))));
-    w_out[n.c] = df2d(df_sub(wpre[n.c], df_mul(K.gz, df_sub(p0, P(n.zm)))));
-    if (pdf && p64) p64[n.c] = df2d(p0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jj[u];
+      if (j < 0) continue;
+      const uint32_t t = t0 + u * stride;
+      if (j == 0 || j == (int)ny) {
+        v_out[t] = df2d(vp[u]);
+        if (j == (int)ny) continue;
+      } else {
+        v_out[t] = df2d(df_sub(vp[u], df_mul(K.gy, df_sub(p0[u], pym[u]))));
+      }
+      const size_t c = cc[u];
+      u_out[c] = df2d(df_sub(up[u], df_mul(K.gx, df_sub(p0[u], pxm[u]))));
+      w_out[c] = df2d(df_sub(wp[u], df_mul(K.gz, df_sub(p0[u], pzm[u]))));
+      if (pdf && p64) p64[c] = df2d(p0[u]);
+    }
   }
 }
 
@@ -101,12 +142,19 @@ __global__ void __launch_bounds__(256) k_df_to_d(const df* __restrict__ a, doubl
     out[i] = df2d(a[i]);
 }
 
-// Test of the residual r_s = f - L p after s-1 corrections (slot s = iter):
-// converged if ||r_s||_inf <= tol ||f||_inf; otherwise ask for correction s if
-// s <= smax, else stop unconverged.  `sweeps` counts applied corrections.
-__global__ void k_refine_check(DevScalars* sc, int smax, cudaGraphConditionalHandle handle, int use_handle) {
+// Test of a residual and the loop decision.
+//  off = 0 (probe): slot s = iter holds r after s-1 corrections.  Converged if
+//    ||r||_inf <= tol ||f||_inf; else correction s follows if s <= smax.
+//  off = 1 (after the fused correction): slot s = iter + 1 holds r after
+//    `iter` corrections.  Converged as above; else another correction follows
+//    if iter < smax (iter is advanced).
+// `sweeps` counts applied corrections; `cont` (and the graph condition) asks
+// for another round.
+__global__ void k_refine_check(DevScalars* sc, int smax, int off, cudaGraphConditionalHandle handle,
+                               int use_handle) {
   if (threadIdx.x != 0) return;
-  const int s = sc->iter;
+  const int it = sc->iter;
+  const int s = it + off;
   const double r = __longlong_as_double((long long)sc->rmax_bits[s]);
   const double f = __longlong_as_double((long long)sc->fmax_bits);
   sc->last_slot = s;
@@ -114,15 +162,102 @@ __global__ void k_refine_check(DevScalars* sc, int smax, cudaGraphConditionalHan
   if (r <= sc->tol * f) {
     sc->done = 1;
     sc->sweeps = s - 1;
-  } else if (s <= smax) {
+  } else if (off == 0 && s <= smax) {
     sc->sweeps = s;
     sc->iter = s + 1;
     cont = 1;
+  } else if (off == 1 && it < smax) {
+    sc->sweeps = it;
+    sc->iter = it + 1;
+    cont = 1;
   } else {
-    sc->sweeps = smax;
+    sc->sweeps = (off == 1) ? it : smax;
   }
   sc->cont = cont;
   if (use_handle) cudaGraphSetConditional(handle, cont);
+}
+
+__global__ void k_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w) {
+  if (threadIdx.x == 0) {
+    sc->out_p = p;
+    sc->out_u = u;
+    sc->out_v = v;
+    sc->out_w = w;
+  }
+}
+
+// Eq. (33) from u_pre as in k_correct_pre, with p as pairs, plus the residual
+// r = f - L p of that same p at every cell (max into rmax[iter + 1]), so that the
+// convergence test after a correction needs no separate pass.
+__global__ void __launch_bounds__(256) k_correct_check(GridDev g, const df* __restrict__ upre,
+                                                       const df* __restrict__ vpre, const df* __restrict__ wpre,
+                                                       const df* __restrict__ pdf, const df* __restrict__ fdf,
+                                                       DevScalars* sc) {
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+  const uint32_t total = (uint32_t)g.nz * (ny + 1) * nx;
+  const StencilConst K = sc->K;
+  double* const u_out = sc->out_u;
+  double* const v_out = sc->out_v;
+  double* const w_out = sc->out_w;
+  double* const p_out = sc->out_p;
+  const int slot = sc->iter + 1;
+  float vmax = 0.0f;
+  constexpr int U = 2;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
+    df vp[U], up[U], wp[U], p0[U], pym[U], pxm[U], pzm[U], pyp[U], pxp[U], pzp[U], fv[U];
+    size_t cc[U];
+    int jj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t t = t0 + u * stride;
+      jj[u] = -1;
+      if (t >= total) continue;
+      const uint32_t r = fdiv(t, g.fd_nx);
+      const int i = (int)(t - r * nx);
+      const int k = (int)fdiv(r, g.fd_nyp1);
+      const int j = (int)(r - (uint32_t)k * (ny + 1));
+      jj[u] = j;
+      vp[u] = vpre[t];
+      if (j < (int)ny) {
+        const Nbr n = neighbours(g, i, j, k);
+        cc[u] = n.c;
+        up[u] = upre[n.c];
+        wp[u] = wpre[n.c];
+        p0[u] = pdf[n.c];
+        pxm[u] = pdf[n.xm];
+        pzm[u] = pdf[n.zm];
+        pxp[u] = pdf[n.xp];
+        pzp[u] = pdf[n.zp];
+        pym[u] = (j > 0) ? pdf[n.c - nx] : p0[u];
+        pyp[u] = (j + 1 < (int)ny) ? pdf[n.c + nx] : p0[u];
+        fv[u] = fdf[n.c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jj[u];
+      if (j < 0) continue;
+      const uint32_t t = t0 + u * stride;
+      if (j == 0 || j == (int)ny) {
+        v_out[t] = df2d(vp[u]);
+        if (j == (int)ny) continue;
+      } else {
+        v_out[t] = df2d(df_sub(vp[u], df_mul(K.gy, df_sub(p0[u], pym[u]))));
+      }
+      const size_t c = cc[u];
+      const df q = p0[u];
+      u_out[c] = df2d(df_sub(up[u], df_mul(K.gx, df_sub(q, pxm[u]))));
+      w_out[c] = df2d(df_sub(wp[u], df_mul(K.gz, df_sub(q, pzm[u]))));
+      p_out[c] = df2d(q);
+      const df lx = df_sub(df_sub(pxp[u], q), df_sub(q, pxm[u]));
+      const df ly = df_sub(df_sub(pyp[u], q), df_sub(q, pym[u]));
+      const df lz = df_sub(df_sub(pzp[u], q), df_sub(q, pzm[u]));
+      const df lap = df_add(df_add(df_mul(lx, K.lx), df_mul(ly, K.ly)), df_mul(lz, K.lz));
+      vmax = fmaxf(vmax, fabsf(df_sub(fv[u], lap).hi));
+    }
+  }
+  block_max_to(&sc->rmax_bits[slot], vmax);
 }
 
 __global__ void k_make_const(GridDev g, DevScalars* sc, double dt) {
@@ -178,14 +313,26 @@ cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const Dev
   return cudaGetLastError();
 }
 
+cudaError_t launch_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w, cudaStream_t st) {
+  k_set_outputs<<<1, 32, 0, st>>>(sc, p, u, v, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct_check(const GridDev& g, const df* upre, const df* vpre, const df* wpre, const df* pdf,
+                                 const df* fdf, DevScalars* sc, cudaStream_t st) {
+  const size_t total = (size_t)g.nz * (g.ny + 1) * g.nx;
+  k_correct_check<<<grid_for(total, (size_t)152 * 64), 256, 0, st>>>(g, upre, vpre, wpre, pdf, fdf, sc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st) {
   k_df_to_d<<<grid_for(n, (size_t)152 * 32), 256, 0, st>>>(a, out, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine_check(DevScalars* sc, int smax, cudaGraphConditionalHandle handle, int use_handle,
-                                cudaStream_t st) {
-  k_refine_check<<<1, 32, 0, st>>>(sc, smax, handle, use_handle);
+cudaError_t launch_refine_check(DevScalars* sc, int smax, int off, cudaGraphConditionalHandle handle,
+                                int use_handle, cudaStream_t st) {
+  k_refine_check<<<1, 32, 0, st>>>(sc, smax, off, handle, use_handle);
   return cudaGetLastError();
 }
 

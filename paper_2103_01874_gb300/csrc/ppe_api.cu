@@ -28,7 +28,12 @@ struct ppe_plan_s {
   void* spec;         // cpx<T>[nz][ny][nxh]
   void* tw_x;         // cpx<T>[nx]: exp(-2 pi i t/nx)
   void* tw_z;         // cpx<T>[nz]
-  void* tab;          // T: elimination multipliers
+  void* tab;          // T: elimination multipliers (FP64 form)
+  RadixPlan rp_y;     // ny (FP32 form: DCT along y)
+  void* tw_y;         // cpx<T>[ny]: exp(-2 pi i t/ny)
+  void* wq_y;         // cpx<T>[ny]: exp(-i pi k/(2 ny))
+  void* lam;          // T[nxh + ny + nz]: eigenvalue parts lam_x, lam_y, lam_z
+  int tky;            // kx columns per CTA of the y DCT pass
   int* line_off;
   int* line_len;
   double a_y;         // 1/dy^2
@@ -39,8 +44,10 @@ struct ppe_plan_s {
   df* vpre;           //   ... on y faces
   df* wpre;           //   ... on z faces
   DevScalars* sc;
-  // refinement loop as a CUDA graph with a WHILE conditional node (FP32_REFINE)
+  // refinement loops as CUDA graphs with a WHILE conditional node (FP32_REFINE):
+  // ppe_solve's and ppe_project's (the latter ends with the fused correction)
   cudaGraphExec_t refine_exec;
+  cudaGraphExec_t project_exec;
   // ppe_project_host staging (allocated on first use)
   double* io[12];
   size_t workspace;
@@ -185,6 +192,41 @@ ppe_status make_thomas(ppe_plan_t P) {
 }
 
 // lines per CTA of the x passes: the largest power of two <= 2048/nx, in [1, 64]
+// Eigenvalue parts of the 7-point operator (FP64 on the host, rounded to T):
+// lam_x(kx) = -(4/dx^2) sin^2(pi kx/nx), lam_y(ky) = -(4/dy^2) sin^2(pi ky/(2 ny)),
+// lam_z(kz) = -(4/dz^2) sin^2(pi kz/nz), and the quarter-wave factors of the DCT.
+template <typename T>
+ppe_status make_dct_tables(ppe_plan_t P) {
+  const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz, nxh = P->nxh;
+  const double dx = P->g.lx / nx, dy = P->g.ly / ny, dz = P->g.lz / nz;
+  std::vector<T> lam(nxh + ny + nz);
+  for (int k = 0; k < nxh; ++k) {
+    const double s = sin_pi_frac(k, nx);
+    lam[k] = (T)(-(4.0 / (dx * dx)) * s * s);
+  }
+  for (int k = 0; k < ny; ++k) {
+    const double s = sin_pi_frac(k, 2 * ny);
+    lam[nxh + k] = (T)(-(4.0 / (dy * dy)) * s * s);
+  }
+  for (int k = 0; k < nz; ++k) {
+    const double s = sin_pi_frac(k, nz);
+    lam[nxh + ny + k] = (T)(-(4.0 / (dz * dz)) * s * s);
+  }
+  std::vector<cpx<T>> wq(ny);
+  for (int k = 0; k < ny; ++k) {
+    double re, im;
+    cis_neg(k, 4 * ny, &re, &im);  // exp(-2 pi i k/(4 ny)) = exp(-i pi k/(2 ny))
+    wq[k].x = (T)re;
+    wq[k].y = (T)im;
+  }
+  ppe_status s;
+  if ((s = upload(&P->lam, lam)) != PPE_OK) return s;
+  if ((s = upload(&P->wq_y, wq)) != PPE_OK) return s;
+  if ((s = make_twiddles<T>(&P->tw_y, ny)) != PPE_OK) return s;
+  P->workspace += lam.size() * sizeof(T) + 2 * sizeof(cpx<T>) * ny;
+  return PPE_OK;
+}
+
 int choose_lpb(int nx) {
   int l = 1;
   while (2 * l <= 2048 / nx && 2 * l <= 64) l *= 2;
@@ -204,7 +246,7 @@ ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_E
 enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
                 K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
-                                           "k_xfwd_resid", "k_zfft_fwd", "k_ythomas", "k_zfft_inv",
+                                           "k_xfwd_resid", "k_zfft_fwd", "k_ysolve", "k_zfft_inv",
                                            "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
                                            "k_df_to_d"};
 constexpr int kProfMax = 16384;
@@ -271,8 +313,14 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   cpx<T>* spec = (cpx<T>*)P->spec;
   const double scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
   PPE_LAUNCH(P, K_ZFFT_FWD, launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
-  PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y, sc,
-                                             P->stream));
+  if (P->fp32) {
+    const T* lam = (const T*)P->lam;
+    PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
+                                            lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->stream));
+  } else {
+    PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y,
+                                               sc, P->stream));
+  }
   PPE_LAUNCH(P, K_ZFFT_INV, launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
   PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
              launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
@@ -280,21 +328,48 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   return PPE_OK;
 }
 
-// One refinement step of PPE_FP32_REFINE: residual r_s = f - L p (pairs) into
-// slot sc->iter, then the convergence test.
-ppe_status refine_probe(ppe_plan_t P, cudaGraphConditionalHandle h, int use_handle) {
+// Refinement sequences of PPE_FP32_REFINE (after the first FP32 solve left p
+// in pdf).  Residuals go into slot sc->iter (see k_refine_check).
+//   REF_SOLVE   (ppe_solve):   probe; WHILE(cont) { p += L^{-1} r; probe }
+//               probe = residual r = f - L p with its x transform, test.
+//   REF_PROJECT (ppe_project): WHILE(cont) { r = f - L p + x transform;
+//               p += L^{-1} r; Eq. (33) correction fused with the residual of
+//               the new p; test }  -- at least one correction, and the test
+//               after the last correction needs no separate residual pass.
+enum RefMode { REF_SOLVE = 0, REF_PROJECT = 1 };
+
+ppe_status resid_fwd(ppe_plan_t P) {
   StencilIn in;
   memset(&in, 0, sizeof(in));
   PPE_LAUNCH(P, K_XFWD_RESID, launch_xfwd<float>(SRC_RESID, true, P->gd, in, P->sc, -1, P->fdf, P->pdf,
                                                  (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x,
                                                  P->lpb, P->stream));
-  PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, h, use_handle, P->stream));
   return PPE_OK;
 }
 
-// Builds the refinement graph once per plan (it touches plan-owned buffers
-// only):  probe; WHILE(cont) { delta = L^{-1} r (FP32); p += delta; probe }.
-ppe_status build_refine_graph(ppe_plan_t P) {
+ppe_status refine_probe(ppe_plan_t P, cudaGraphConditionalHandle h, int use_handle) {
+  ppe_status s = resid_fwd(P);
+  if (s != PPE_OK) return s;
+  PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, 0, h, use_handle, P->stream));
+  return PPE_OK;
+}
+
+ppe_status refine_body(ppe_plan_t P, int mode, cudaGraphConditionalHandle h, int use_handle) {
+  ppe_status s;
+  if (mode == REF_SOLVE) {
+    if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) return s;
+    return refine_probe(P, h, use_handle);
+  }
+  if ((s = resid_fwd(P)) != PPE_OK) return s;
+  if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) return s;
+  PPE_LAUNCH(P, K_CORRECT, launch_correct_check(P->gd, P->upre, P->vpre, P->wpre, P->pdf, P->fdf, P->sc, P->stream));
+  PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, 1, h, use_handle, P->stream));
+  return PPE_OK;
+}
+
+// Builds a refinement graph once per plan (it touches plan-owned buffers and
+// the device scalar block only): [probe]; WHILE(cond) { body }.
+ppe_status build_refine_graph(ppe_plan_t P, int mode, cudaGraphExec_t* exec) {
   cudaStream_t saved = P->stream;
   const int saved_prof = P->prof_on;
   cudaStream_t cs = nullptr;
@@ -311,12 +386,15 @@ ppe_status build_refine_graph(ppe_plan_t P) {
   };
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(PPE_ERR_CUDA);
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
-  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  // REF_PROJECT runs its body at least once: the condition starts at 1
+  if (cudaGraphConditionalHandleCreate(&h, g, mode == REF_PROJECT ? 1u : 0u, cudaGraphCondAssignDefault) !=
+      cudaSuccess)
+    return fail(PPE_ERR_CUDA);
   P->stream = cs;
   P->prof_on = 0;
   if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(PPE_ERR_CUDA);
-  st = refine_probe(P, h, 1);
+  if (mode == REF_SOLVE) st = refine_probe(P, h, 1);
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -342,12 +420,11 @@ ppe_status build_refine_graph(ppe_plan_t P) {
   if (st != PPE_OK) return fail(st);
   if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(PPE_ERR_CUDA);
-  st = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false);
-  if (st == PPE_OK) st = refine_probe(P, h, 1);
+  st = refine_body(P, mode, h, 1);
   cudaGraph_t outb = nullptr;
   if (cudaStreamEndCapture(cs, &outb) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
   if (st != PPE_OK) return fail(st);
-  if (cudaGraphInstantiate(&P->refine_exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
   P->stream = saved;
   P->prof_on = saved_prof;
   cudaGraphDestroy(g);
@@ -355,24 +432,43 @@ ppe_status build_refine_graph(ppe_plan_t P) {
   return PPE_OK;
 }
 
-// The refinement loop once pdf holds the first FP32 solve.  Normally one graph
-// launch (the loop runs on the device); while per-kernel profiling is on, the
-// same kernels are launched from the host, reading the test result after each
-// check so that no empty sweep is launched.
-ppe_status refine(ppe_plan_t P) {
+ppe_status build_refine_graphs(ppe_plan_t P) {
+  if (P->refine_exec) cudaGraphExecDestroy(P->refine_exec);
+  if (P->project_exec) cudaGraphExecDestroy(P->project_exec);
+  P->refine_exec = nullptr;
+  P->project_exec = nullptr;
+  ppe_status s = build_refine_graph(P, REF_SOLVE, &P->refine_exec);
+  if (s == PPE_OK) s = build_refine_graph(P, REF_PROJECT, &P->project_exec);
+  return s;
+}
+
+// Runs a refinement sequence.  Normally one graph launch (the loop runs on the
+// device); while per-kernel profiling is on, the same kernels are launched from
+// the host, which reads the test result after each check.
+ppe_status refine(ppe_plan_t P, int mode) {
+  if (mode == REF_PROJECT && P->opt.max_sweeps == 0) {
+    cudaGraphConditionalHandle none = 0;
+    PPE_LAUNCH(P, K_CORRECT, launch_correct_check(P->gd, P->upre, P->vpre, P->wpre, P->pdf, P->fdf, P->sc,
+                                                  P->stream));
+    PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, 0, 1, none, 0, P->stream));
+    return PPE_OK;
+  }
   if (!P->prof_on) {
-    PPE_TRY(cudaGraphLaunch(P->refine_exec, P->stream));
+    PPE_TRY(cudaGraphLaunch(mode == REF_SOLVE ? P->refine_exec : P->project_exec, P->stream));
     return PPE_OK;
   }
   cudaGraphConditionalHandle none = 0;
-  ppe_status s = refine_probe(P, none, 0);
+  ppe_status s = (mode == REF_SOLVE) ? refine_probe(P, none, 0) : PPE_OK;
+  bool first = true;
   while (s == PPE_OK) {
-    int cont = 0;
-    PPE_TRY(cudaMemcpyAsync(&cont, &P->sc->cont, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-    PPE_TRY(cudaStreamSynchronize(P->stream));
-    if (!cont) break;
-    if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) break;
-    s = refine_probe(P, none, 0);
+    if (!(mode == REF_PROJECT && first)) {
+      int cont = 0;
+      PPE_TRY(cudaMemcpyAsync(&cont, &P->sc->cont, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      PPE_TRY(cudaStreamSynchronize(P->stream));
+      if (!cont) break;
+    }
+    first = false;
+    s = refine_body(P, mode, none, 0);
   }
   return s;
 }
@@ -381,10 +477,8 @@ ppe_status refine(ppe_plan_t P) {
 // shared memory lets two CTAs share an SM, else one.
 void choose_rhs_tiles(ppe_plan_t P) {
   const int nx = P->g.nx;
-  auto sm = [&](int tj) { return P->fp32 ? rhs_smem<float>(nx, tj) : rhs_smem<double>(nx, tj); };
   int tj = 4;
-  while (tj > 1 && sm(tj) > 110 * 1024) tj /= 2;
-  if (sm(tj) > 110 * 1024) tj = 1;
+  while (tj > 1 && rhs_smem(nx, tj) > 110 * 1024) tj /= 2;
   P->tj = tj;
   P->kc = P->g.nz < 16 ? P->g.nz : 16;
 }
@@ -418,7 +512,7 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   const size_t n = (size_t)g->nx * g->ny * g->nz;
   const size_t nxh = g->nx / 2 + 1;
   size_t b = cb * nxh * g->ny * g->nz + cb * (g->nx + g->nz) + sizeof(DevScalars);
-  if (fp32) b += 16 * n;                                                 // f, p as pairs
+  b += (fp32 ? 16 : 8) * n;                                             // f (and p) as pairs
   b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
   return b;
@@ -473,6 +567,8 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->rp_z = radix_plan(g->nz);
   P->lpb = choose_lpb(g->nx);
   P->tkx = choose_tkx(g->nz, P->fp32);
+  P->tky = choose_tkx(g->ny, P->fp32);
+  P->rp_y = radix_plan(g->ny);
   P->cplx_bytes = P->fp32 ? 8 : 16;
 
   ppe_status s = PPE_OK;
@@ -480,19 +576,19 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   s = alloc_status(cudaMalloc(&P->spec, nspec * P->cplx_bytes));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->sc, sizeof(DevScalars)));
   const size_t ncell = (size_t)g->nx * g->ny * g->nz, nvf = (size_t)g->nx * (g->ny + 1) * g->nz;
-  if (s == PPE_OK && P->fp32) s = alloc_status(cudaMalloc((void**)&P->fdf, sizeof(df) * ncell));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->fdf, sizeof(df) * ncell));
   if (s == PPE_OK && P->fp32) s = alloc_status(cudaMalloc((void**)&P->pdf, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
-  P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 * sizeof(df) * ncell : 0) +
+  P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 : 1) * sizeof(df) * ncell +
                  sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz);
   choose_rhs_tiles(P);
   if (s == PPE_OK) {
     if (P->fp32) {
       s = make_twiddles<float>(&P->tw_x, g->nx);
       if (s == PPE_OK) s = make_twiddles<float>(&P->tw_z, g->nz);
-      if (s == PPE_OK) s = make_thomas<float>(P);
+      if (s == PPE_OK) s = make_dct_tables<float>(P);
       if (s == PPE_OK) s = cuda_status(set_smem_limits<float>());
     } else {
       s = make_twiddles<double>(&P->tw_x, g->nx);
@@ -501,7 +597,7 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       if (s == PPE_OK) s = cuda_status(set_smem_limits<double>());
     }
   }
-  if (s == PPE_OK && P->fp32) s = build_refine_graph(P);
+  if (s == PPE_OK && P->fp32) s = build_refine_graphs(P);
   if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, 1.0, o.refine_tol, 0, P->stream));
   // grid-only constants (1/dx^2 ...) for a ppe_solve that no ppe_rhs preceded
   if (s == PPE_OK) s = cuda_status(launch_make_const(P->gd, P->sc, 1.0, P->stream));
@@ -526,6 +622,9 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->tw_x);
   cudaFree(P->tw_z);
   cudaFree(P->tab);
+  cudaFree(P->tw_y);
+  cudaFree(P->wq_y);
+  cudaFree(P->lam);
   cudaFree(P->line_off);
   cudaFree(P->line_len);
   cudaFree(P->fdf);
@@ -535,12 +634,49 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->wpre);
   cudaFree(P->sc);
   if (P->refine_exec) cudaGraphExecDestroy(P->refine_exec);
+  if (P->project_exec) cudaGraphExecDestroy(P->project_exec);
   for (int i = 0; i < 12; ++i) cudaFree(P->io[i]);
   if (P->prof_ev)
     for (cudaEvent_t e : *P->prof_ev) cudaEventDestroy(e);
   delete P->prof_ev;
   delete P->prof_name;
   delete P;
+}
+
+ppe_status ppe_get_tuning(ppe_plan_t P, ppe_tuning* t) {
+  if (!P || !t) return PPE_ERR_INVALID_ARG;
+  t->rhs_lines = P->tj;
+  t->rhs_planes = P->kc;
+  t->x_lines = P->lpb;
+  t->z_cols = P->tkx;
+  t->y_cols = P->tky;
+  return PPE_OK;
+}
+
+ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
+  if (!P || !t) return PPE_ERR_INVALID_ARG;
+  auto pow2 = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
+  const size_t lim = 227 * 1024;
+  const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
+  if (!pow2(t->rhs_lines, 1, 8) || rhs_smem(nx, t->rhs_lines) > lim) return PPE_ERR_INVALID_ARG;
+  if (t->rhs_planes < 1 || t->rhs_planes > nz) return PPE_ERR_INVALID_ARG;
+  if (!pow2(t->x_lines, 1, 64)) return PPE_ERR_INVALID_ARG;
+  if (!pow2(t->z_cols, 1, 16) || !pow2(t->y_cols, 1, 32)) return PPE_ERR_INVALID_ARG;
+  const size_t xs = P->fp32 ? (xfwd_smem<float>(nx, t->x_lines) > xinv_smem<float>(nx, t->x_lines)
+                                   ? xfwd_smem<float>(nx, t->x_lines) : xinv_smem<float>(nx, t->x_lines))
+                            : (xfwd_smem<double>(nx, t->x_lines) > xinv_smem<double>(nx, t->x_lines)
+                                   ? xfwd_smem<double>(nx, t->x_lines) : xinv_smem<double>(nx, t->x_lines));
+  const size_t zs = P->fp32 ? zfft_smem<float>(nz, t->z_cols) : zfft_smem<double>(nz, t->z_cols);
+  const size_t ys = P->fp32 ? zfft_smem<float>(ny, t->y_cols) : 0;
+  if (xs > lim || zs > lim || ys > lim) return PPE_ERR_INVALID_ARG;
+  PPE_TRY(cudaStreamSynchronize(P->stream));
+  P->tj = t->rhs_lines;
+  P->kc = t->rhs_planes;
+  P->lpb = t->x_lines;
+  P->tkx = t->z_cols;
+  P->tky = t->y_cols;
+  if (P->fp32) return build_refine_graphs(P);
+  return PPE_OK;
 }
 
 ppe_status ppe_profile(ppe_plan_t P, int enable) {
@@ -583,12 +719,7 @@ ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double*
   PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, rho0, P->opt.refine_tol, 0, P->stream));
   if (!(rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(rho, n, P->sc, P->stream));
   PPE_TRY(launch_make_const(P->gd, P->sc, dt, P->stream));
-  if (P->fp32)
-    PPE_LAUNCH(P, K_RHS, launch_rhs<float>(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                           P->rp_half, (const cpx<float>*)P->tw_x, P->tj, P->kc, P->stream));
-  else
-    PPE_LAUNCH(P, K_RHS, launch_rhs<double>(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                            P->rp_half, (const cpx<double>*)P->tw_x, P->tj, P->kc, P->stream));
+  PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, P->tj, P->kc, P->stream));
   return PPE_OK;
 }
 
@@ -604,7 +735,7 @@ ppe_status ppe_solve(ppe_plan_t P, const double* f, double* p) {
                                                (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->lpb,
                                                P->stream));
     if ((s = solve_tail<float>(P, XI_DF, nullptr, P->pdf, false)) != PPE_OK) return s;
-    if ((s = refine(P)) != PPE_OK) return s;
+    if ((s = refine(P, REF_SOLVE)) != PPE_OK) return s;
     PPE_LAUNCH(P, K_DF_TO_D,
                launch_df_to_d(P->pdf, p, (size_t)P->g.nx * P->g.ny * P->g.nz, P->stream));
     return PPE_OK;
@@ -639,17 +770,20 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
   PPE_TRY(launch_make_const(P->gd, P->sc, F->dt, P->stream));
   ppe_status s;
   if (P->fp32) {
-    PPE_LAUNCH(P, K_RHS, launch_rhs<float>(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre,
-                                           (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->tj,
-                                           P->kc, P->stream));
+    PPE_TRY(launch_set_outputs(P->sc, F->p, F->u_out, F->v_out, F->w_out, P->stream));
+    PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre, P->tj, P->kc,
+                                    P->stream));
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr,
+                                               (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->lpb,
+                                               P->stream));
     if ((s = solve_tail<float>(P, XI_DF, nullptr, P->pdf, false)) != PPE_OK) return s;
-    if ((s = refine(P)) != PPE_OK) return s;
-    PPE_LAUNCH(P, K_CORRECT, launch_correct_pre(P->gd, F->dt, P->upre, P->vpre, P->wpre, P->pdf, F->p, P->sc,
-                                                F->u_out, F->v_out, F->w_out, P->stream));
+    if ((s = refine(P, REF_PROJECT)) != PPE_OK) return s;
   } else {
-    PPE_LAUNCH(P, K_RHS, launch_rhs<double>(P->gd, in, P->sc, F->f, nullptr, P->upre, P->vpre, P->wpre,
-                                            (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->tj,
-                                            P->kc, P->stream));
+    PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre, P->tj, P->kc,
+                                    P->stream));
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr,
+                                                (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->lpb,
+                                                P->stream));
     if ((s = solve_tail<double>(P, XI_F64, F->p, nullptr, false)) != PPE_OK) return s;
     PPE_LAUNCH(P, K_CORRECT, launch_correct_pre(P->gd, F->dt, P->upre, P->vpre, P->wpre, nullptr, F->p, P->sc,
                                                 F->u_out, F->v_out, F->w_out, P->stream));

@@ -38,6 +38,10 @@ struct DevScalars {
   int sweeps;                                   // sweeps run
   double tol;                                   // refinement tolerance (relative)
   StencilConst K;                               // stencil constants of the current call
+  double* out_p;                                // ppe_project outputs, set per call (k_set_outputs)
+  double* out_u;
+  double* out_v;
+  double* out_w;
 };
 
 struct GridDev {
@@ -62,17 +66,13 @@ struct StencilIn {
   int face_rule;     // 0 arithmetic, 1 harmonic
 };
 
-enum XSource { SRC_F = 1, SRC_RESID = 2 };
+enum XSource { SRC_F = 1, SRC_RESID = 2, SRC_FDF = 3 };
 enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
 
 // ---- launchers (k_rhs.cu) ----
-template <typename T>
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
-                       df* vpre, df* wpre, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, int tj, int kc,
-                       cudaStream_t st);
-template <typename T>
+                       df* vpre, df* wpre, int tj, int kc, cudaStream_t st);
 size_t rhs_smem(int nx, int tj);
-template <typename T>
 cudaError_t set_rhs_smem_limit();
 
 // ---- launchers (k_spectral.cu) ----
@@ -86,6 +86,9 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
 template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* line_off,
                            const int* line_len, T a, const DevScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, const cpx<T>* wq,
+                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, cudaStream_t st);
 template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp_half, const cpx<T>* tw_x, int lpb, const DevScalars* sc,
@@ -114,9 +117,17 @@ cudaError_t launch_correct_pre(const GridDev& g, double dt, const df* upre, cons
 cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const DevScalars* sc, double* u_out,
                                 double* v_out, double* w_out, cudaStream_t st);
 cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st);
-// Convergence test of the residual in slot sc->iter; sets sc->cont and, when
-// use_handle, the WHILE condition of the refinement graph.
-cudaError_t launch_refine_check(DevScalars* sc, int smax, cudaGraphConditionalHandle handle, int use_handle,
-                                cudaStream_t st);
+// Writes the per-call output pointers of ppe_project into sc (so that graphs
+// captured once can run with any outputs).
+cudaError_t launch_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w, cudaStream_t st);
+// Eq. (33) from u_pre and p (pairs) fused with the residual r = f - L p of the
+// same p into rmax[iter + 1]; outputs through sc->out_*.
+cudaError_t launch_correct_check(const GridDev& g, const df* upre, const df* vpre, const df* wpre, const df* pdf,
+                                 const df* fdf, DevScalars* sc, cudaStream_t st);
+// Convergence test of the residual in slot sc->iter + off (off = 0: probe
+// before a correction; off = 1: after correction sc->iter, from the fused
+// correction kernel); sets sc->cont and, when use_handle, the WHILE condition.
+cudaError_t launch_refine_check(DevScalars* sc, int smax, int off, cudaGraphConditionalHandle handle,
+                                int use_handle, cudaStream_t st);
 
 }  // namespace ppe

@@ -45,6 +45,14 @@ class Info(ctypes.Structure):
     _fields_ = [("sweeps", c_int), ("rel_residual", c_double), ("f_max", c_double), ("rho0", c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("rhs_lines", c_int), ("rhs_planes", c_int), ("x_lines", c_int), ("z_cols", c_int),
+                ("y_cols", c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int), ("total_ms", c_double)]
 
@@ -73,6 +81,8 @@ SIGNATURES = {
     "ppe_size_supported": (c_int, [c_int, c_int, c_int]),
     "ppe_profile": (c_int, [c_void_p, c_int]),
     "ppe_rho0_noalloc": (c_int, [c_void_p, c_size_t, c_void_p, c_void_p]),
+    "ppe_get_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
+    "ppe_set_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
 }
 
@@ -242,6 +252,18 @@ class Plan:
             return inf
         _check(code, "ppe_get_info")
         return inf
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().ppe_get_tuning(self._h, ctypes.byref(t)), "ppe_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        """Change launch shapes (ppe_set_tuning); unspecified fields keep their value."""
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = Tuning(**cur)
+        _check(lib().ppe_set_tuning(self._h, ctypes.byref(t)), "ppe_set_tuning")
 
     def profile(self, enable: bool):
         _check(lib().ppe_profile(self._h, 1 if enable else 0), "ppe_profile")

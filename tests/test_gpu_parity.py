@@ -168,3 +168,34 @@ def test_errors():
 
 
 from _gpu_util import dev_fields, project_gpu, to_dev  # noqa: E402
+
+
+@pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
+def test_tuning_does_not_change_results(precision):
+    """Launch shapes (tile sizes, marching chunk) change no bit of the outputs,
+    including ragged last tiles; invalid shapes are rejected."""
+    import torch
+    fl = fields.make_fields(48, 24, 36, seed=17, recipe="multimode", width=4.0)
+    d = dev_fields(fl)
+    shapes = [dict(rhs_lines=4, rhs_planes=16, x_lines=32, z_cols=8, y_cols=16),
+              dict(rhs_lines=1, rhs_planes=5, x_lines=1, z_cols=1, y_cols=1),
+              dict(rhs_lines=8, rhs_planes=36, x_lines=64, z_cols=16, y_cols=32),
+              dict(rhs_lines=2, rhs_planes=7, x_lines=4, z_cols=2, y_cols=4)]
+    outs = []
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=precision) as plan:
+        for sh in shapes:
+            plan.set_tuning(**sh)
+            assert plan.get_tuning() == sh
+            o = [torch.empty(fl.shape, dtype=torch.float64, device="cuda"), torch.empty_like(d["u"]),
+                 torch.empty_like(d["v"]), torch.empty_like(d["w"])]
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, *o)
+            torch.cuda.synchronize()
+            outs.append([t.cpu().numpy() for t in o])
+        with pytest.raises(ppe.PPEError):
+            plan.set_tuning(rhs_lines=3)
+        with pytest.raises(ppe.PPEError):
+            plan.set_tuning(rhs_planes=0)
+        assert plan.get_tuning() == shapes[-1]
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
