@@ -149,6 +149,48 @@ PPE_HD df df_recip(df a) {
 }
 PPE_HD float df_to_f(df a) { return a.hi + a.lo; }
 
+// "Lazy" variants for chains of operations: the hi parts are combined exactly
+// (TwoSum / TwoProd) and the low parts are summed in plain FP32, without the
+// renormalising FastTwoSum after each step.  The result is an unnormalised
+// pair whose low part stays tiny against the high part; its error is that of
+// the normalised operation plus a few ulps of the low part (relative ~2^-47).
+// Normalise (df_norm) before storing or converting.
+PPE_HD df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
+PPE_HD df df_addz(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return s;
+}
+PPE_HD df df_subz(df a, df b) { return df_addz(a, df_neg(b)); }
+PPE_HD df df_mulz(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return p;
+}
+PPE_HD df df_mulz_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = fmaf(a.lo, b, p.lo);
+  return p;
+}
+// Approximate float reciprocal seed (about 1 ulp on the device; exact on the host).
+PPE_HD float rcp_seed(float x) {
+#ifdef __CUDA_ARCH__
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return 1.0f / x;
+#endif
+}
+// 1/a as an unnormalised pair: seed y0 ~ 1/a.hi, one Newton step (relative
+// error ~ seed error squared, about 2^-44 with the device seed)
+PPE_HD df df_recipz(df a) {
+  const float y0 = rcp_seed(a.hi);
+  df p = two_prod(a.hi, y0);
+  const float e = ((1.0f - p.hi) - p.lo) - a.lo * y0;
+  return {y0, y0 * e};
+}
+
 // IEEE double -> pair (see header comment).  Relative error <= 2^-48.
 PPE_HD df d2df(double x) {
   const uint64_t b = d_bits(x);

@@ -3,16 +3,20 @@
 // The x and z directions of the grid are periodic, so the constant-coefficient
 // pressure equation (Eq. (34) of the paper, solved directly by a fast Poisson
 // solver as stated after it) is diagonal in the discrete Fourier basis along x
-// and z.  These device routines transform many such lines at once, the lines
-// held in shared memory by one CTA.
+// and z; the y pass uses the same routine inside its cosine transform.  These
+// device routines transform many lines at once, held in shared memory by one
+// CTA.
 //
-// One pass of radix R over a line of length n (Stockham autosort, so no bit
+// One pass of radix R over a line of length n (Stockham autosort, no bit
 // reversal): with Ns the product of the radices already applied, butterfly t
 // (0 <= t < n/R) reads the R elements t + q n/R, multiplies element q by
 // w^(q k n/(Ns R)) with k = t mod Ns and w = exp(-+ 2 pi i / n), takes the
-// R-point DFT and writes output q to (t/Ns) Ns R + k + q Ns.  Passes alternate
-// between two buffers.  Forward transforms use w = exp(-2 pi i/n), inverse
-// ones exp(+2 pi i/n); neither is scaled.
+// R-point DFT in registers and writes output q to (t/Ns) Ns R + k + q Ns.
+// Passes alternate between two buffers.  Radices 16 and 8 are built from 4x4
+// and 2x4 in registers (Cooley-Tukey), so a 256-point line takes two passes.
+// Forward transforms use w = exp(-2 pi i/n), inverse ones exp(+2 pi i/n);
+// neither is scaled.  Consecutive threads take consecutive lines (the line
+// index is the fast one), so twiddle reads are warp broadcasts.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -48,6 +52,29 @@ struct RadixPlan {
   FastDiv ns[16];
 };
 
+// exp(-+ 2 pi i m / 16) for a compile-time m, times v.  Multiples of a quarter
+// turn are exact rotations; the others use cos(pi/8), sin(pi/8), sqrt(1/2).
+template <typename T, bool INV, int M16>
+__device__ __forceinline__ cpx<T> tw16(cpx<T> v) {
+  constexpr int m = ((M16 % 16) + 16) % 16;
+  constexpr double C1 = 0.92387953251128675612818318939679;  // cos(pi/8)
+  constexpr double S1 = 0.38268343236508977172845998403040;  // sin(pi/8)
+  constexpr double H = 0.70710678118654752440084436210485;   // sqrt(1/2)
+  // cos(pi m/8), sin(pi m/8)
+  constexpr double c = (m == 0) ? 1 : (m == 1) ? C1 : (m == 2) ? H : (m == 3) ? S1 : (m == 4) ? 0
+                     : (m == 5) ? -S1 : (m == 6) ? -H : (m == 7) ? -C1 : (m == 8) ? -1 : (m == 9) ? -C1
+                     : (m == 10) ? -H : (m == 11) ? -S1 : (m == 12) ? 0 : (m == 13) ? S1 : (m == 14) ? H : C1;
+  constexpr double s = (m == 0) ? 0 : (m == 1) ? S1 : (m == 2) ? H : (m == 3) ? C1 : (m == 4) ? 1
+                     : (m == 5) ? C1 : (m == 6) ? H : (m == 7) ? S1 : (m == 8) ? 0 : (m == 9) ? -S1
+                     : (m == 10) ? -H : (m == 11) ? -C1 : (m == 12) ? -1 : (m == 13) ? -C1 : (m == 14) ? -H : -S1;
+  if (m == 0) return v;
+  if (m == 8) return {-v.x, -v.y};
+  if (m == 4) return rot<T, INV>(v);                 // -i forward
+  if (m == 12) return rot<T, !INV>(v);               // +i forward
+  const T cr = (T)c, si = INV ? (T)s : (T)(-s);      // w = c - i s (forward)
+  return {v.x * cr - v.y * si, v.x * si + v.y * cr};
+}
+
 template <typename T, bool INV, int R> struct SmallDft;
 
 template <typename T, bool INV> struct SmallDft<T, INV, 2> {
@@ -67,7 +94,7 @@ template <typename T, bool INV> struct SmallDft<T, INV, 3> {
     cpx<T> d = csub(v[1], v[2]);
     cpx<T> t3 = {s3 * d.x, s3 * d.y};
     v[0] = cadd(v[0], t1);
-    cpx<T> r = rot<T, INV>(t3);  // -i t3 forward
+    cpx<T> r = rot<T, INV>(t3);
     v[1] = cadd(t2, r);
     v[2] = csub(t2, r);
   }
@@ -84,30 +111,72 @@ template <typename T, bool INV> struct SmallDft<T, INV, 4> {
   }
 };
 
+// R = R1 R2 from an R1-point and an R2-point DFT: sub-DFTs of size R1 on the
+// stride-R2 subsequences, twiddles w_R^(j2 k1), then size-R2 DFTs:
+// X[k1 + R1 k2] = sum_j2 w_R^(j2 k1) w_R2^(j2 k2) sum_j1 v[j2 + R2 j1] w_R1^(j1 k1).
+template <typename T, bool INV, int R1, int R2>
+__device__ __forceinline__ void dft_ct(cpx<T>* v) {
+  constexpr int R = R1 * R2;
+  cpx<T> a[R];
+#pragma unroll
+  for (int j2 = 0; j2 < R2; ++j2) {
+    cpx<T> s[R1];
+#pragma unroll
+    for (int j1 = 0; j1 < R1; ++j1) s[j1] = v[j2 + R2 * j1];
+    SmallDft<T, INV, R1>::run(s);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[j2 * R1 + k1] = s[k1];
+  }
+  // twiddles w_R^(j2 k1) = w_16^(j2 k1 16/R)
+#pragma unroll
+  for (int j2 = 1; j2 < R2; ++j2) {
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      cpx<T>& x = a[j2 * R1 + k1];
+      const int e = j2 * k1 * (16 / R);
+      switch (e) {  // resolved at compile time after unrolling
+        case 1: x = tw16<T, INV, 1>(x); break;
+        case 2: x = tw16<T, INV, 2>(x); break;
+        case 3: x = tw16<T, INV, 3>(x); break;
+        case 4: x = tw16<T, INV, 4>(x); break;
+        case 6: x = tw16<T, INV, 6>(x); break;
+        case 8: x = tw16<T, INV, 8>(x); break;
+        case 9: x = tw16<T, INV, 9>(x); break;
+        case 12: x = tw16<T, INV, 12>(x); break;
+        default: break;
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cpx<T> s[R2];
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) s[j2] = a[j2 * R1 + k1];
+    SmallDft<T, INV, R2>::run(s);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = s[k2];
+  }
+}
+
+template <typename T, bool INV> struct SmallDft<T, INV, 8> {
+  static __device__ __forceinline__ void run(cpx<T>* v) { dft_ct<T, INV, 2, 4>(v); }
+};
+template <typename T, bool INV> struct SmallDft<T, INV, 16> {
+  static __device__ __forceinline__ void run(cpx<T>* v) { dft_ct<T, INV, 4, 4>(v); }
+};
+
 // One Stockham pass over nl = 2^nl_log2 lines (nl <= blockDim.x, blockDim.x a
-// power of two).  Line `l`, element `e` lives at base[l*ls + e*es].  With
-// line_fastest, consecutive threads take consecutive lines (suits lines that
-// are interleaved in memory, es > 1); otherwise each line gets blockDim/nl
-// consecutive threads.  No integer division: shifts, masks and a
-// multiply-high divider for Ns.
+// power of two).  Line `l`, element `e` lives at base[l*ls + e*es].
+// Consecutive threads take consecutive lines.  `tw` (shared memory) holds
+// exp(-2 pi i t / (n*tws)), t < n*tws.
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst, int nl_log2,
                                               int n, int ls, int es, int Ns, const FastDiv& nsdiv,
-                                              const cpx<T>* __restrict__ tw, int tws, bool line_fastest) {
+                                              const cpx<T>* __restrict__ tw, int tws) {
   const int nb = n / R;
   const int tstep = n / (Ns * R);
-  const int bl = __ffs(blockDim.x) - 1;
-  int line, t0, ts;
-  if (line_fastest) {
-    line = threadIdx.x & ((1 << nl_log2) - 1);
-    t0 = threadIdx.x >> nl_log2;
-    ts = blockDim.x >> nl_log2;
-  } else {
-    const int tl = bl - nl_log2;  // log2 threads per line
-    line = threadIdx.x >> tl;
-    t0 = threadIdx.x & ((1 << tl) - 1);
-    ts = 1 << tl;
-  }
+  const int line = threadIdx.x & ((1 << nl_log2) - 1);
+  const int t0 = threadIdx.x >> nl_log2, ts = blockDim.x >> nl_log2;
   const cpx<T>* s = src + line * ls;
   cpx<T>* d = dst + line * ls;
   for (int t = t0; t < nb; t += ts) {
@@ -117,10 +186,10 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = s[(t + q * nb) * es];
     if (Ns > 1) {
-      const int e1 = tstep * k;
+      const int e1 = tstep * k * tws;
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        cpx<T> w = tw[(q * e1) * tws];
+        cpx<T> w = tw[q * e1];
         if (INV) w.y = -w.y;
         v[q] = cmul(v[q], w);
       }
@@ -134,20 +203,20 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* __restrict__ src, cp
 
 // Full transform of 2^nl_log2 lines held in `a` (with `b` as the second
 // buffer).  The caller synchronises before the call; the routine synchronises
-// after every pass and returns the buffer that holds the result.  `tw` is the
-// table exp(-2 pi i t / (n*tws)), t < n*tws.
+// after every pass and returns the buffer that holds the result.
 template <typename T, bool INV>
 __device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, int nl_log2, const RadixPlan& rp, int ls, int es,
-                             const cpx<T>* __restrict__ tw, int tws, bool line_fastest) {
+                             const cpx<T>* __restrict__ tw, int tws) {
   int Ns = 1;
   for (int s = 0; s < rp.nst; ++s) {
     const int R = rp.r[s];
-    if (R == 4)
-      stockham_pass<T, INV, 4>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
-    else if (R == 2)
-      stockham_pass<T, INV, 2>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
-    else
-      stockham_pass<T, INV, 3>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws, line_fastest);
+    switch (R) {
+      case 16: stockham_pass<T, INV, 16>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws); break;
+      case 8: stockham_pass<T, INV, 8>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws); break;
+      case 4: stockham_pass<T, INV, 4>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws); break;
+      case 2: stockham_pass<T, INV, 2>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws); break;
+      default: stockham_pass<T, INV, 3>(a, b, nl_log2, rp.n, ls, es, Ns, rp.ns[s], tw, tws); break;
+    }
     __syncthreads();
     cpx<T>* t = a;
     a = b;
@@ -155,6 +224,91 @@ __device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, int nl_log2, const RadixPlan&
     Ns *= R;
   }
   return a;
+}
+
+// ---------------------------------------------------------------------------
+// Compile-time-length variant.  With n, the radices, Ns and n/R known to the
+// compiler, every per-element index and twiddle offset becomes an immediate or
+// one multiply-add, and the butterfly loop bounds are constants.  Same passes
+// and results as fft_lines; used for the lengths of the common grids.
+// ---------------------------------------------------------------------------
+namespace ctfft {
+
+// The radix sequence of radix_plan() (host): radix 16 while it divides (if
+// maxr >= 16), one 8 (if maxr >= 8), 4s, one 2, then 3s.
+__host__ __device__ constexpr int radix_at(int n, int s, int maxr) {
+  int m = n, i = 0;
+  while (maxr >= 16 && m % 16 == 0) { if (i == s) return 16; m /= 16; ++i; }
+  if (maxr >= 8 && m % 8 == 0) { if (i == s) return 8; m /= 8; ++i; }
+  while (m % 4 == 0) { if (i == s) return 4; m /= 4; ++i; }
+  if (m % 2 == 0) { if (i == s) return 2; m /= 2; ++i; }
+  while (m % 3 == 0) { if (i == s) return 3; m /= 3; ++i; }
+  return 1;
+}
+__host__ __device__ constexpr int nst(int n, int maxr) {
+  int s = 0;
+  while (radix_at(n, s, maxr) != 1) ++s;
+  return s;
+}
+__host__ __device__ constexpr int ns_at(int n, int s, int maxr) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= radix_at(n, i, maxr);
+  return p;
+}
+
+template <typename T, bool INV, int N, int S, int MAXR, int TWS>
+__device__ __forceinline__ void pass_ct(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst, int nl_log2,
+                                        int ls, int es, const cpx<T>* __restrict__ tw) {
+  constexpr int R = radix_at(N, S, MAXR);
+  constexpr int NS = ns_at(N, S, MAXR);
+  constexpr int NB = N / R;
+  constexpr int TSTEP = N / (NS * R);
+  const int line = threadIdx.x & ((1 << nl_log2) - 1);
+  const int t0 = threadIdx.x >> nl_log2, ts = blockDim.x >> nl_log2;
+  const cpx<T>* s = src + line * ls;
+  cpx<T>* d = dst + line * ls;
+  const int sb = NB * es, sq = NS * es;
+  for (int t = t0; t < NB; t += ts) {
+    const int q0 = t / NS, k = t - q0 * NS;  // NS a power of 2 times 3^b, known here
+    cpx<T> v[R];
+    const cpx<T>* sp = s + t * es;
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = sp[q * sb];
+    if (NS > 1) {
+      const int e1 = TSTEP * TWS * k;
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        cpx<T> w = tw[q * e1];
+        if (INV) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
+    }
+    SmallDft<T, INV, R>::run(v);
+    cpx<T>* dp = d + (q0 * NS * R + k) * es;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dp[q * sq] = v[q];
+  }
+}
+
+template <typename T, bool INV, int N, int S, int MAXR, int TWS>
+__device__ __forceinline__ cpx<T>* run_from(cpx<T>* a, cpx<T>* b, int nl_log2, int ls, int es,
+                                            const cpx<T>* __restrict__ tw) {
+  if constexpr (S >= nst(N, MAXR)) {
+    return a;
+  } else {
+    pass_ct<T, INV, N, S, MAXR, TWS>(a, b, nl_log2, ls, es, tw);
+    __syncthreads();
+    return run_from<T, INV, N, S + 1, MAXR, TWS>(b, a, nl_log2, ls, es, tw);
+  }
+}
+
+}  // namespace ctfft
+
+// fft_lines for a compile-time length N (radices up to MAXR, twiddle stride TWS)
+template <typename T, bool INV, int N, int MAXR, int TWS>
+__device__ __forceinline__ cpx<T>* fft_lines_ct(cpx<T>* a, cpx<T>* b, int nl_log2, int ls, int es,
+                                                const cpx<T>* __restrict__ tw) {
+  return ctfft::run_from<T, INV, N, 0, MAXR, TWS>(a, b, nl_log2, ls, es, tw);
 }
 
 }  // namespace ppe

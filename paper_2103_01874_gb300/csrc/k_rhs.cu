@@ -3,8 +3,9 @@
 //   f = D[beta_f G p_hat] + (rho_0/dt)(D u* - S),  beta_f = 1 - rho_0/rho_f,
 //   p_hat = 2 p^n - p^{n-1}                                        (Eq. (32))
 //
-// Written per face as Q_f = beta_f (G p_hat)_f + (rho_0/dt) u*_f, so that
-// f = D Q - (rho_0/dt) S.  The same face quantity also gives the explicitly
+// Written per face as Q~_f = beta_f (p_hat_R - p_hat_L) + (rho_0/dt) h u*_f (h
+// the spacing of the face's direction), so that f = sum_dir (Q~_+ - Q~_-)/h^2
+// - (rho_0/dt) S.  The same face quantity also gives the explicitly
 // split velocity of Eq. (33):  since 1/rho_f - 1/rho_0 = -beta_f/rho_0,
 //   u^{n+1}_f = u*_f + (dt/rho_0) beta_f (G p_hat)_f - (dt/rho_0) (G p^{n+1})_f
 // and this kernel stores u_pre_f = u*_f + (dt/rho_0) beta_f (G p_hat)_f, leaving
@@ -53,8 +54,9 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
   df* QZ = QY + (tj + 1) * nx;                      // [2][tj][nx]
 
   const StencilConst K = sc->K;  // formed once per call by k_make_const
-  const size_t plane = (size_t)ny * nx;
-  const size_t vplane = (size_t)(ny + 1) * nx;
+  // 32-bit element offsets (grids up to 1024^3 stay below 2^32)
+  const uint32_t plane = (uint32_t)ny * (uint32_t)nx;
+  const uint32_t vplane = (uint32_t)(ny + 1) * (uint32_t)nx;
 
   // Loops below take their items in chunks of U per thread and issue all of a
   // chunk's global loads before the first use, so that a CTA waits about once
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         vm[u] = 0.0;
         vr[u] = 1.0;
         if (idx < total && j >= 0 && j < ny) {
-          const size_t c = (size_t)kk * plane + (size_t)j * nx + i;
+          const uint32_t c = (uint32_t)kk * plane + (uint32_t)(j * nx + i);
           vn[u] = __ldg(in.pn + c);
           vm[u] = __ldg(in.pnm1 + c);
           vr[u] = __ldg(in.rho + c);
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int idx = b0 + u * nthr + threadIdx.x;
         const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
         ws[u] = 0.0;
-        if (idx < total && j0 + jj < ny) ws[u] = __ldg(in.w + (size_t)kf * plane + (size_t)(j0 + jj) * nx + i);
+        if (idx < total && j0 + jj < ny) ws[u] = __ldg(in.w + ((uint32_t)kf * plane + (uint32_t)((j0 + jj) * nx + i)));
       }
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
@@ -123,10 +125,9 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         df q = {0.0f, 0.0f};
         if (j < ny) {
           const int r = (jj + 1) * nx + i;
-          const df flux = df_mul(df_mul(beta_df(Rl[r], Rh[r], K, rule), df_sub(Ph[r], Pl[r])), K.idz);
-          const df us = d2df(ws[u]);
-          q = df_add(flux, df_mul(K.c, us));
-          if (owned && out.wpre) out.wpre[(size_t)kf * plane + (size_t)j * nx + i] = df_add(us, df_mul(K.g, flux));
+          const FaceOut fo = face_q(Rl[r], Rh[r], Pl[r], Ph[r], d2df(ws[u]), K.cz, K.gz, K, rule);
+          q = fo.q;
+          if (owned && out.wpre) out.wpre[(uint32_t)kf * plane + (uint32_t)(j * nx + i)] = fo.upre;
         }
         QZ[zs * tj * nx + idx] = q;
       }
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int idx = b0 + u * nthr + threadIdx.x;
         const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
         us_[u] = 0.0;
-        if (idx < tj * nx && j0 + jj < ny) us_[u] = __ldg(in.u + (size_t)k * plane + (size_t)(j0 + jj) * nx + i);
+        if (idx < tj * nx && j0 + jj < ny) us_[u] = __ldg(in.u + ((uint32_t)k * plane + (uint32_t)((j0 + jj) * nx + i)));
       }
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
@@ -169,12 +170,9 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         if (j < ny) {
           const int r = (jj + 1) * nx;
           const int im = (i == 0) ? nx - 1 : i - 1;
-          const df flux =
-              df_mul(df_mul(beta_df(Ra[r + im], Ra[r + i], K, rule), df_sub(Pa[r + i], Pa[r + im])), K.idx);
-          const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-          const df us = d2df(us_[u]);
-          q = df_add(flux, df_mul(K.c, us));
-          if (out.upre) out.upre[c] = df_add(us, df_mul(K.g, flux));
+          const FaceOut fo = face_q(Ra[r + im], Ra[r + i], Pa[r + im], Pa[r + i], d2df(us_[u]), K.cx, K.gx, K, rule);
+          q = fo.q;
+          if (out.upre) out.upre[(uint32_t)k * plane + (uint32_t)(j * nx + i)] = fo.upre;
         }
         QX[idx] = q;
       }
@@ -186,7 +184,7 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int idx = b0 + u * nthr + threadIdx.x;
         const int jf = (int)fdiv(idx, g.fd_nx), i = idx - jf * nx;
         vs_[u] = 0.0;
-        if (idx < (tj + 1) * nx && j0 + jf <= ny) vs_[u] = __ldg(in.v + (size_t)k * vplane + (size_t)(j0 + jf) * nx + i);
+        if (idx < (tj + 1) * nx && j0 + jf <= ny) vs_[u] = __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)((j0 + jf) * nx + i)));
       }
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
@@ -196,17 +194,17 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int j = j0 + jf;  // face between cells j-1 and j
         df q = {0.0f, 0.0f};
         if (j <= ny) {
-          const size_t cv = (size_t)k * vplane + (size_t)j * nx + i;
+          const uint32_t cv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
           const df vs = d2df(vs_[u]);
           const bool own = (jf < tj) || (j == ny);
           if (j == 0 || j == ny) {
-            q = df_mul(K.c, vs);
+            q = df_norm(df_mulz(K.cy, vs));
             if (own && out.vpre) out.vpre[cv] = vs;
           } else {
             const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
-            const df flux = df_mul(df_mul(beta_df(Ra[rl], Ra[rh], K, rule), df_sub(Pa[rh], Pa[rl])), K.idy);
-            q = df_add(flux, df_mul(K.c, vs));
-            if (own && out.vpre) out.vpre[cv] = df_add(vs, df_mul(K.g, flux));
+            const FaceOut fo = face_q(Ra[rl], Ra[rh], Pa[rl], Pa[rh], vs, K.cy, K.gy, K, rule);
+            q = fo.q;
+            if (own && out.vpre) out.vpre[cv] = fo.upre;
           }
         }
         QY[idx] = q;
@@ -222,7 +220,7 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int idx = b0 + u * nthr + threadIdx.x;
         const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
         ss_[u] = 0.0;
-        if (idx < tj * nx && j0 + jj < ny) ss_[u] = __ldg(in.S + (size_t)k * plane + (size_t)(j0 + jj) * nx + i);
+        if (idx < tj * nx && j0 + jj < ny) ss_[u] = __ldg(in.S + ((uint32_t)k * plane + (uint32_t)((j0 + jj) * nx + i)));
       }
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
@@ -232,11 +230,12 @@ __global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevS
         const int j = j0 + jj;
         if (j < ny) {
           const int ip = (i + 1 == nx) ? 0 : i + 1;
-          const df dxq = df_mul(df_sub(QX[jj * nx + ip], QX[idx]), K.idx);
-          const df dyq = df_mul(df_sub(QY[(jj + 1) * nx + i], QY[idx]), K.idy);
-          const df dzq = df_mul(df_sub(QZ[zup * tj * nx + idx], QZ[zdn * tj * nx + idx]), K.idz);
-          const size_t c = (size_t)k * plane + (size_t)j * nx + i;
-          const df f = df_sub(df_add(df_add(dxq, dyq), dzq), df_mul(K.c, d2df(ss_[u])));
+          // f = sum over directions of (Q~_+ - Q~_-) / h^2 - (rho_0/dt) S
+          const df dxq = df_mulz(df_subz(QX[jj * nx + ip], QX[idx]), K.lx);
+          const df dyq = df_mulz(df_subz(QY[(jj + 1) * nx + i], QY[idx]), K.ly);
+          const df dzq = df_mulz(df_subz(QZ[zup * tj * nx + idx], QZ[zdn * tj * nx + idx]), K.lz);
+          const uint32_t c = (uint32_t)k * plane + (uint32_t)(j * nx + i);
+          const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, d2df(ss_[u]))));
           if (out.fdf) out.fdf[c] = f;
           if (out.f64) out.f64[c] = df2d(f);
           vmax = fmaxf(vmax, fabsf(f.hi));

@@ -16,6 +16,8 @@
 //   k_xinv    one CTA per `lpb` lines: half spectrum -> real line, scaled, and
 //             stored to p (FP64), stored as pairs, or added to the pairs
 //             (refinement update).
+#include <type_traits>
+
 #include "async.cuh"
 #include "dfloat.cuh"
 #include "ppe_internal.h"
@@ -31,20 +33,67 @@ __device__ __forceinline__ cpx<T> ld_tw(const cpx<T>* tw, int t) {
 // log2 of a power of two
 __device__ __forceinline__ int ilog2_dev(int v) { return __ffs(v) - 1; }
 
+// Transform with the compile-time-length passes when N > 0 (FP32 common
+// lengths), else with the run-time-length ones.  MAXR matches radix_plan().
+template <typename T, bool INV, int N, int TWS>
+__device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int nl_log2, const RadixPlan& rp, int ls, int es,
+                                          const cpx<T>* __restrict__ tw) {
+  if constexpr (N > 0) {
+    return fft_lines_ct<T, INV, N, (sizeof(T) == 4 ? 16 : 8), TWS>(a, b, nl_log2, ls, es, tw);
+  } else {
+    return fft_lines<T, INV>(a, b, nl_log2, rp, ls, es, tw, TWS);
+  }
+}
+
+// Calls f(std::integral_constant<int, N>) with N = n for the lengths that have
+// compile-time instances (FP32 only), N = 0 otherwise.
+template <typename T, typename F>
+cudaError_t with_len(int n, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    switch (n) {
+      case 16: return f(std::integral_constant<int, 16>{});
+      case 24: return f(std::integral_constant<int, 24>{});
+      case 32: return f(std::integral_constant<int, 32>{});
+      case 48: return f(std::integral_constant<int, 48>{});
+      case 64: return f(std::integral_constant<int, 64>{});
+      case 96: return f(std::integral_constant<int, 96>{});
+      case 128: return f(std::integral_constant<int, 128>{});
+      case 192: return f(std::integral_constant<int, 192>{});
+      case 256: return f(std::integral_constant<int, 256>{});
+      case 384: return f(std::integral_constant<int, 384>{});
+      default: break;
+    }
+  }
+  return f(std::integral_constant<int, 0>{});
+}
+
+// Kernels needing more than the default 48 KB of dynamic shared memory opt in.
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // ---------------------------------------------------------------------------
 // forward x pass
 // ---------------------------------------------------------------------------
-template <typename T, int SRC, bool DO_FFT>
+template <typename T, int SRC, bool DO_FFT, int N>
 __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
                                               const df* __restrict__ pdf, cpx<T>* spec, RadixPlan rp,
                                               const cpx<T>* __restrict__ tw, int lpb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
+  const int lsc = M + 1;  // padded line stride (complex elements) against bank conflicts
   const int nlines = g.ny * g.nz;
   const int l0 = blockIdx.x * lpb;
-  T* line_re = reinterpret_cast<T*>(smem_raw);                       // lpb * nx reals == lpb * M complex
-  cpx<T>* bufb = reinterpret_cast<cpx<T>*>(smem_raw + sizeof(T) * (size_t)lpb * nx);
+  cpx<T>* bufa = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb lines of lsc; line ll holds its nx reals packed
+  cpx<T>* bufb = bufa + (size_t)lpb * lsc;
+  cpx<T>* tws = bufb + (size_t)lpb * lsc;           // twiddles exp(-2 pi i t/nx), t < nx
+  T* line_re = reinterpret_cast<T*>(bufa);
+  if (DO_FFT) {
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) cp_async<sizeof(cpx<T>)>(&tws[t], &tw[t]);
+  }
 
   df lc[3];
   if (SRC == SRC_RESID) {
@@ -70,18 +119,27 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         }
         vmax = fmaxf(vmax, fabsf(d2df(x).hi));
       }
-      line_re[idx] = val;
+      line_re[idx + ll * 2] = val;  // line ll starts at 2*ll*lsc = ll*nx + 2*ll
     }
   } else if (SRC == SRC_FDF) {
-    // f as pairs, written by the right-hand-side kernel (which also took ||f||)
-    for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
-      const int ll = (int)fdiv(idx, g.fd_nx);
-      T val = (T)0;
-      if (l0 + ll < nlines) {
-        const df v = fdf[(size_t)l0 * nx + idx];
-        val = (sizeof(T) == 8) ? (T)df2d(v) : (T)df_to_f(v);
+    // f as pairs, written by the right-hand-side kernel (which also took ||f||);
+    // four loads per thread in flight before the first use
+    constexpr int U = 4;
+    for (int b0 = 0; b0 < lpb * nx; b0 += U * blockDim.x) {
+      df v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x + threadIdx.x;
+        const int ll = (int)fdiv(idx, g.fd_nx);
+        v[u] = (idx < lpb * nx && l0 + ll < nlines) ? fdf[(size_t)l0 * nx + idx] : df{0.0f, 0.0f};
       }
-      line_re[idx] = val;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x + threadIdx.x;
+        if (idx >= lpb * nx) continue;
+        const int ll = (int)fdiv(idx, g.fd_nx);
+        line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d(v[u]) : (T)df_to_f(v[u]);
+      }
     }
   } else {
     // residual r = f - L p in pairs; two cells per thread per round with all
@@ -117,33 +175,34 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         T val = (T)0;
         if (jj[u] >= 0) {
           const df p0 = pc[u];
-          const df lx = df_sub(df_sub(pxp[u], p0), df_sub(p0, pxm[u]));
-          const df lz = df_sub(df_sub(pzp[u], p0), df_sub(p0, pzm[u]));
-          const df ly = df_sub(df_sub(pyp[u], p0), df_sub(p0, pym[u]));  // wall sides contribute 0
-          const df lap = df_add(df_add(df_mul(lx, lc[0]), df_mul(ly, lc[1])), df_mul(lz, lc[2]));
-          const df r = df_sub(fv[u], lap);
-          val = (T)df_to_f(r);
-          vmax = fmaxf(vmax, fabsf(r.hi));
+          const df lx = df_subz(df_subz(pxp[u], p0), df_subz(p0, pxm[u]));
+          const df lz = df_subz(df_subz(pzp[u], p0), df_subz(p0, pzm[u]));
+          const df ly = df_subz(df_subz(pyp[u], p0), df_subz(p0, pym[u]));  // wall sides contribute 0
+          const df lap = df_addz(df_addz(df_mulz(lx, lc[0]), df_mulz(ly, lc[1])), df_mulz(lz, lc[2]));
+          const float r = df_to_f(df_subz(fv[u], lap));
+          val = (T)r;
+          vmax = fmaxf(vmax, fabsf(r));
         }
-        line_re[idx] = val;
+        line_re[idx + (int)fdiv(idx, g.fd_nx) * 2] = val;
       }
     }
   }
   if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
   if (!DO_FFT) return;
+  cp_async_wait_all();
   __syncthreads();
-  cpx<T>* z = fft_lines<T, false>(reinterpret_cast<cpx<T>*>(line_re), bufb, ilog2_dev(lpb), rp, M, 1, tw, 2, false);
+  cpx<T>* z = fft_any<T, false, N, 2>(bufa, bufb, ilog2_dev(lpb), rp, lsc, 1, tws);
   // untangle: X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, W = exp(-2 pi i/nx)
   for (int idx = threadIdx.x; idx < lpb * nxh; idx += blockDim.x) {
     const int ll = (int)fdiv(idx, g.fd_nxh), kx = idx - ll * nxh;
     const int line = l0 + ll;
     if (line >= nlines) continue;
-    const cpx<T> zk = z[ll * M + (kx == M ? 0 : kx)];
-    const cpx<T> zc = z[ll * M + (kx == 0 ? 0 : M - kx)];
+    const cpx<T> zk = z[ll * lsc + (kx == M ? 0 : kx)];
+    const cpx<T> zc = z[ll * lsc + (kx == 0 ? 0 : M - kx)];
     const cpx<T> a = {zk.x + zc.x, zk.y - zc.y};
     const cpx<T> b = {zk.x - zc.x, zk.y + zc.y};
-    const cpx<T> wb = cmul(ld_tw(tw, kx), b);
+    const cpx<T> wb = cmul(tws[kx], b);
     cpx<T> X;
     X.x = (T)0.5 * (a.x + wb.y);
     X.y = (T)0.5 * (a.y - wb.x);
@@ -154,7 +213,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
 // ---------------------------------------------------------------------------
 // z pass
 // ---------------------------------------------------------------------------
-template <typename T, bool INV>
+template <typename T, bool INV, int N>
 __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
                                               int tkx, const DevScalars* sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -165,6 +224,8 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
   const int kx0 = (blockIdx.x - j * ntile) * tkx;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* b = a + (size_t)tkx * nz;
+  cpx<T>* tws = b + (size_t)tkx * nz;  // exp(-2 pi i t/nz)
+  for (int t = threadIdx.x; t < nz; t += blockDim.x) cp_async<sizeof(cpx<T>)>(&tws[t], &tw[t]);
   const size_t rowstride = (size_t)g.ny * nxh;
   const size_t base = (size_t)j * nxh + kx0;
   const int tl2 = ilog2_dev(tkx);
@@ -177,7 +238,7 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
   }
   cp_async_wait_all();
   __syncthreads();
-  cpx<T>* r = fft_lines<T, INV>(a, b, tl2, rp, 1, tkx, tw, 1, true);
+  cpx<T>* r = fft_any<T, INV, N, 1>(a, b, tl2, rp, 1, tkx, tws);
   for (int idx = threadIdx.x; idx < nz * tkx; idx += blockDim.x) {
     const int k = idx >> tl2, c = idx & (tkx - 1);
     if (kx0 + c < nxh) spec[base + k * rowstride + c] = r[idx];
@@ -296,7 +357,7 @@ __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const 
 // V_N = V_0.  The inverse takes V'_k = conj(w_k)(P_k - i P_{N-k}), P_N = 0,
 // an inverse FFT, and x_j = v'[pos(j)] / N.  Eigenvalue of mode (kx, ky, kz):
 // lam_x[kx] + lam_y[ky] + lam_z[kz]; the zero mode is set to zero.
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
                                               const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
                                               const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky) {
@@ -306,6 +367,8 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
   const int kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * tky;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* b = a + (size_t)tky * ny;
+  cpx<T>* tws = b + (size_t)tky * ny;  // exp(-2 pi i t/ny)
+  for (int t = threadIdx.x; t < ny; t += blockDim.x) cp_async<sizeof(cpx<T>)>(&tws[t], &tw[t]);
   const int t2 = ilog2_dev(tky);
   const size_t base = (size_t)kz * ny * nxh + kx0;
   for (int idx = threadIdx.x; idx < ny * tky; idx += blockDim.x) {
@@ -318,7 +381,7 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
   }
   cp_async_wait_all();
   __syncthreads();
-  cpx<T>* V = fft_lines<T, false>(a, b, t2, rp, 1, tky, tw, 1, true);
+  cpx<T>* V = fft_any<T, false, N, 1>(a, b, t2, rp, 1, tky, tws);
   const T inv_n = (T)1 / (T)ny;
   const T lz = lam_z[kz];
   const int npair = ny / 2 + 1;
@@ -350,7 +413,7 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
   }
   __syncthreads();
   cpx<T>* W = (V == a) ? b : a;
-  cpx<T>* R = fft_lines<T, true>(V, W, t2, rp, 1, tky, tw, 1, true);
+  cpx<T>* R = fft_any<T, true, N, 1>(V, W, t2, rp, 1, tky, tws);
   for (int idx = threadIdx.x; idx < ny * tky; idx += blockDim.x) {
     const int j = idx >> t2, c = idx & (tky - 1);
     const int pj = (j & 1) ? ny - 1 - (j >> 1) : (j >> 1);
@@ -362,17 +425,20 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
 // inverse x pass
 // ---------------------------------------------------------------------------
 // MODE: XI_F64 p = s x (FP64); XI_DF pdf = s x (pairs); XI_DF_ACC pdf += s x
-template <typename T, int MODE>
+template <typename T, int MODE, int N>
 __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, df* pdf,
                                               double scale, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
                                               const DevScalars* sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
+  const int lsc = M + 1;  // line stride (complex): nxh values, also the padded FFT stride
   const int nlines = g.ny * g.nz;
   const int l0 = blockIdx.x * lpb;
-  cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb * M
-  cpx<T>* b = a + (size_t)lpb * M;                  // lpb * (M + 1)
+  cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb * lsc
+  cpx<T>* b = a + (size_t)lpb * lsc;                // lpb * lsc
+  cpx<T>* tws = b + (size_t)lpb * lsc;              // exp(-2 pi i t/nx), t < nx
+  for (int t = threadIdx.x; t < nx; t += blockDim.x) cp_async<sizeof(cpx<T>)>(&tws[t], &tw[t]);
   for (int idx = threadIdx.x; idx < lpb * nxh; idx += blockDim.x) {
     const int ll = (int)fdiv(idx, g.fd_nxh);
     const int line = l0 + ll;
@@ -386,23 +452,23 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
   // Z_k = E_k + i O_k, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(W^k)/2
   for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
     const int ll = (int)fdiv(idx, g.fd_m), k = idx - ll * M;
-    const cpx<T> xk = b[ll * nxh + k];
-    const cpx<T> xc = b[ll * nxh + (M - k)];
+    const cpx<T> xk = b[ll * lsc + k];
+    const cpx<T> xc = b[ll * lsc + (M - k)];
     const cpx<T> e = {(T)0.5 * (xk.x + xc.x), (T)0.5 * (xk.y - xc.y)};
     cpx<T> dd = {(T)0.5 * (xk.x - xc.x), (T)0.5 * (xk.y + xc.y)};
-    cpx<T> w = ld_tw(tw, k);
+    cpx<T> w = tws[k];
     w.y = -w.y;
     const cpx<T> o = cmul(dd, w);
-    a[idx] = {e.x - o.y, e.y + o.x};
+    a[ll * lsc + k] = {e.x - o.y, e.y + o.x};
   }
   __syncthreads();
-  cpx<T>* z = fft_lines<T, true>(a, b, ilog2_dev(lpb), rp, M, 1, tw, 2, false);
+  cpx<T>* z = fft_any<T, true, N, 2>(a, b, ilog2_dev(lpb), rp, lsc, 1, tws);
   const df sdf = d2df(scale);
   for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
     const int ll = (int)fdiv(idx, g.fd_m), n = idx - ll * M;
     const int line = l0 + ll;
     if (line >= nlines) continue;
-    const cpx<T> v = z[idx];
+    const cpx<T> v = z[ll * lsc + n];
     const size_t o = (size_t)line * nx + 2 * n;
     if (MODE == XI_F64) {
       p[o] = scale * (double)v.x;
@@ -425,35 +491,20 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
 // ---------------------------------------------------------------------------
 template <typename T>
 size_t xfwd_smem(int nx, int lpb) {
-  return sizeof(T) * (size_t)lpb * nx + sizeof(cpx<T>) * (size_t)lpb * (nx / 2);
+  return sizeof(cpx<T>) * (2 * (size_t)lpb * (nx / 2 + 1) + (size_t)nx);
 }
 template <typename T>
 size_t zfft_smem(int nz, int tkx) {
-  return 2 * sizeof(cpx<T>) * (size_t)tkx * nz;
+  return sizeof(cpx<T>) * (2 * (size_t)tkx * nz + (size_t)nz);
 }
 template <typename T>
 size_t xinv_smem(int nx, int lpb) {
-  return sizeof(cpx<T>) * (size_t)lpb * (nx / 2) + sizeof(cpx<T>) * (size_t)lpb * (nx / 2 + 1);
+  return sizeof(cpx<T>) * (2 * (size_t)lpb * (nx / 2 + 1) + (size_t)nx);
 }
 
 template <typename T>
 cudaError_t set_smem_limits() {
-  const int lim = 227 * 1024;
-  cudaError_t e = cudaSuccess;
-#define PPE_SET(K) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-  PPE_SET((k_xfwd<T, SRC_F, true>));
-  PPE_SET((k_xfwd<T, SRC_FDF, true>));
-  PPE_SET((k_xfwd<T, SRC_RESID, true>));
-  PPE_SET((k_xfwd<T, SRC_RESID, false>));
-  PPE_SET((k_zfft<T, false>));
-  PPE_SET((k_zfft<T, true>));
-  PPE_SET((k_ythomas<T>));
-  PPE_SET((k_ydct<T>));
-  PPE_SET((k_xinv<T, XI_F64>));
-  PPE_SET((k_xinv<T, XI_DF>));
-  PPE_SET((k_xinv<T, XI_DF_ACC>));
-#undef PPE_SET
+  cudaError_t e = cudaFuncSetAttribute(k_ythomas<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess) e = set_rhs_smem_limit();
   return e;
 }
@@ -464,16 +515,25 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
                         cudaStream_t st) {
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
-  const size_t sm = do_fft ? xfwd_smem<T>(g.nx, lpb) : sizeof(T) * (size_t)lpb * g.nx;
-  if (src == SRC_F)
-    k_xfwd<T, SRC_F, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-  else if (src == SRC_FDF)
-    k_xfwd<T, SRC_FDF, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-  else if (do_fft)
-    k_xfwd<T, SRC_RESID, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-  else
-    k_xfwd<T, SRC_RESID, false><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-  return cudaGetLastError();
+  const size_t sm = xfwd_smem<T>(g.nx, lpb);
+  return with_len<T>(g.nx / 2, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    cudaError_t e;
+    if (src == SRC_F) {
+      if ((e = allow_smem(k_xfwd<T, SRC_F, true, N>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_F, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    } else if (src == SRC_FDF) {
+      if ((e = allow_smem(k_xfwd<T, SRC_FDF, true, N>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_FDF, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    } else if (do_fft) {
+      if ((e = allow_smem(k_xfwd<T, SRC_RESID, true, N>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_RESID, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    } else {
+      if ((e = allow_smem(k_xfwd<T, SRC_RESID, false, 0>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_RESID, false, 0><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    }
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
@@ -482,11 +542,18 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
   const int nxh = g.nx / 2 + 1;
   const int grid = g.ny * ((nxh + tkx - 1) / tkx);
   const size_t sm = zfft_smem<T>(g.nz, tkx);
-  if (inverse)
-    k_zfft<T, true><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
-  else
-    k_zfft<T, false><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
-  return cudaGetLastError();
+  return with_len<T>(g.nz, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    cudaError_t e;
+    if (inverse) {
+      if ((e = allow_smem(k_zfft<T, true, N>, sm)) != cudaSuccess) return e;
+      k_zfft<T, true, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
+    } else {
+      if ((e = allow_smem(k_zfft<T, false, N>, sm)) != cudaSuccess) return e;
+      k_zfft<T, false, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
+    }
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
@@ -517,8 +584,14 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
                         const T* lam_x, const T* lam_y, const T* lam_z, int tky, cudaStream_t st) {
   const int nxh = g.nx / 2 + 1;
   const int grid = g.nz * ((nxh + tky - 1) / tky);
-  k_ydct<T><<<grid, 256, zfft_smem<T>(g.ny, tky), st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky);
-  return cudaGetLastError();
+  const size_t sm = zfft_smem<T>(g.ny, tky);
+  return with_len<T>(g.ny, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    cudaError_t e = allow_smem(k_ydct<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_ydct<T, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky);
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
@@ -527,13 +600,21 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
   const size_t sm = xinv_smem<T>(g.nx, lpb);
-  if (mode == XI_F64)
-    k_xinv<T, XI_F64><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
-  else if (mode == XI_DF)
-    k_xinv<T, XI_DF><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
-  else
-    k_xinv<T, XI_DF_ACC><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
-  return cudaGetLastError();
+  return with_len<T>(g.nx / 2, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    cudaError_t e;
+    if (mode == XI_F64) {
+      if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
+      k_xinv<T, XI_F64, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+    } else if (mode == XI_DF) {
+      if ((e = allow_smem(k_xinv<T, XI_DF, N>, sm)) != cudaSuccess) return e;
+      k_xinv<T, XI_DF, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+    } else {
+      if ((e = allow_smem(k_xinv<T, XI_DF_ACC, N>, sm)) != cudaSuccess) return e;
+      k_xinv<T, XI_DF_ACC, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+    }
+    return cudaGetLastError();
+  });
 }
 
 #define PPE_INST(T)                                                                                              \

@@ -94,11 +94,11 @@ __global__ void __launch_bounds__(256) k_correct_pre(GridDev g, double dt, const
         v_out[t] = df2d(vp[u]);
         if (j == (int)ny) continue;
       } else {
-        v_out[t] = df2d(df_sub(vp[u], df_mul(K.gy, df_sub(p0[u], pym[u]))));
+        v_out[t] = df2d(df_subz(vp[u], df_mulz(K.gy, df_subz(p0[u], pym[u]))));
       }
       const size_t c = cc[u];
-      u_out[c] = df2d(df_sub(up[u], df_mul(K.gx, df_sub(p0[u], pxm[u]))));
-      w_out[c] = df2d(df_sub(wp[u], df_mul(K.gz, df_sub(p0[u], pzm[u]))));
+      u_out[c] = df2d(df_subz(up[u], df_mulz(K.gx, df_subz(p0[u], pxm[u]))));
+      w_out[c] = df2d(df_subz(wp[u], df_mulz(K.gz, df_subz(p0[u], pzm[u]))));
       if (pdf && p64) p64[c] = df2d(p0[u]);
     }
   }
@@ -127,13 +127,13 @@ __global__ void __launch_bounds__(256) k_correct_full(GridDev g, StencilIn in, c
     const df p0 = d2df(in.p[n.c]), h0 = phat_df(in.pn, in.pnm1, n.c), r0 = d2df(__ldg(in.rho + n.c));
     auto face = [&](size_t cn, const df& gk) -> df {
       const df b = beta_df(d2df(__ldg(in.rho + cn)), r0, K, rule);
-      const df gp = df_sub(p0, d2df(in.p[cn]));
-      const df gh = df_sub(h0, phat_df(in.pn, in.pnm1, cn));
-      return df_mul(gk, df_sub(gp, df_mul(b, gh)));
+      const df gp = df_subz(p0, d2df(in.p[cn]));
+      const df gh = df_subz(h0, phat_df(in.pn, in.pnm1, cn));
+      return df_mulz(gk, df_subz(gp, df_mulz(b, gh)));
     };
-    if (j > 0) v_out[cv] = df2d(df_sub(d2df(in.v[cv]), face(n.c - nx, K.gy)));
-    u_out[n.c] = df2d(df_sub(d2df(in.u[n.c]), face(n.xm, K.gx)));
-    w_out[n.c] = df2d(df_sub(d2df(in.w[n.c]), face(n.zm, K.gz)));
+    if (j > 0) v_out[cv] = df2d(df_subz(d2df(in.v[cv]), face(n.c - nx, K.gy)));
+    u_out[n.c] = df2d(df_subz(d2df(in.u[n.c]), face(n.xm, K.gx)));
+    w_out[n.c] = df2d(df_subz(d2df(in.w[n.c]), face(n.zm, K.gz)));
   }
 }
 
@@ -189,7 +189,7 @@ __global__ void k_set_outputs(DevScalars* sc, double* p, double* u, double* v, d
 // Eq. (33) from u_pre as in k_correct_pre, with p as pairs, plus the residual
 // r = f - L p of that same p at every cell (max into rmax[iter + 1]), so that the
 // convergence test after a correction needs no separate pass.
-__global__ void __launch_bounds__(256) k_correct_check(GridDev g, const df* __restrict__ upre,
+__global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* __restrict__ upre,
                                                        const df* __restrict__ vpre, const df* __restrict__ wpre,
                                                        const df* __restrict__ pdf, const df* __restrict__ fdf,
                                                        DevScalars* sc) {
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_correct_check(GridDev g, const df* __re
   double* const p_out = sc->out_p;
   const int slot = sc->iter + 1;
   float vmax = 0.0f;
-  constexpr int U = 2;
+  constexpr int U = 1;  // one face per thread and round: 4 CTAs per SM fit the register budget
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
     df vp[U], up[U], wp[U], p0[U], pym[U], pxm[U], pzm[U], pyp[U], pxp[U], pzp[U], fv[U];
@@ -243,18 +243,18 @@ __global__ void __launch_bounds__(256) k_correct_check(GridDev g, const df* __re
         v_out[t] = df2d(vp[u]);
         if (j == (int)ny) continue;
       } else {
-        v_out[t] = df2d(df_sub(vp[u], df_mul(K.gy, df_sub(p0[u], pym[u]))));
+        v_out[t] = df2d(df_subz(vp[u], df_mulz(K.gy, df_subz(p0[u], pym[u]))));
       }
       const size_t c = cc[u];
       const df q = p0[u];
-      u_out[c] = df2d(df_sub(up[u], df_mul(K.gx, df_sub(q, pxm[u]))));
-      w_out[c] = df2d(df_sub(wp[u], df_mul(K.gz, df_sub(q, pzm[u]))));
+      u_out[c] = df2d(df_subz(up[u], df_mulz(K.gx, df_subz(q, pxm[u]))));
+      w_out[c] = df2d(df_subz(wp[u], df_mulz(K.gz, df_subz(q, pzm[u]))));
       p_out[c] = df2d(q);
-      const df lx = df_sub(df_sub(pxp[u], q), df_sub(q, pxm[u]));
-      const df ly = df_sub(df_sub(pyp[u], q), df_sub(q, pym[u]));
-      const df lz = df_sub(df_sub(pzp[u], q), df_sub(q, pzm[u]));
-      const df lap = df_add(df_add(df_mul(lx, K.lx), df_mul(ly, K.ly)), df_mul(lz, K.lz));
-      vmax = fmaxf(vmax, fabsf(df_sub(fv[u], lap).hi));
+      const df lx = df_subz(df_subz(pxp[u], q), df_subz(q, pxm[u]));
+      const df ly = df_subz(df_subz(pyp[u], q), df_subz(q, pym[u]));
+      const df lz = df_subz(df_subz(pzp[u], q), df_subz(q, pzm[u]));
+      const df lap = df_addz(df_addz(df_mulz(lx, K.lx), df_mulz(ly, K.ly)), df_mulz(lz, K.lz));
+      vmax = fmaxf(vmax, fabsf(df_to_f(df_subz(fv[u], lap))));
     }
   }
   block_max_to(&sc->rmax_bits[slot], vmax);

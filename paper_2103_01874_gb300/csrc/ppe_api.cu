@@ -70,13 +70,17 @@ bool is_23_smooth(int n) {
 
 bool dim_ok(int n) { return n >= 8 && n <= kMaxDim && is_23_smooth(n); }
 
-RadixPlan radix_plan(int n) {
+// Radix sequence: radix 16 while it divides (up to maxr), one 8, 4s, one 2,
+// then 3s -- the fewest shared-memory passes for 2^a 3^b.
+RadixPlan radix_plan(int n, int maxr) {
   RadixPlan rp;
   memset(&rp, 0, sizeof(rp));
   rp.n = n;
   int m = n;
+  while (maxr >= 16 && m % 16 == 0) { rp.r[rp.nst++] = 16; m /= 16; }
+  if (maxr >= 8 && m % 8 == 0) { rp.r[rp.nst++] = 8; m /= 8; }
   while (m % 4 == 0) { rp.r[rp.nst++] = 4; m /= 4; }
-  while (m % 2 == 0) { rp.r[rp.nst++] = 2; m /= 2; }
+  if (m % 2 == 0) { rp.r[rp.nst++] = 2; m /= 2; }
   while (m % 3 == 0) { rp.r[rp.nst++] = 3; m /= 3; }
   int ns = 1;
   for (int s = 0; s < rp.nst; ++s) {
@@ -229,14 +233,16 @@ ppe_status make_dct_tables(ppe_plan_t P) {
 
 int choose_lpb(int nx) {
   int l = 1;
-  while (2 * l <= 2048 / nx && 2 * l <= 64) l *= 2;
+  while (2 * l <= 4096 / nx && 2 * l <= 64) l *= 2;
   return l;
 }
 
+// kx columns per CTA of the z and y passes: 8 (64-byte FP32 / 128-byte FP64
+// rows; measured best at 256^3 on a GB300), fewer when the tile would not fit
 int choose_tkx(int nz, bool fp32) {
   const size_t cb = fp32 ? 8 : 16;
-  int t = fp32 ? 16 : 8;
-  while (t > 2 && 2 * cb * (size_t)t * nz > 160 * 1024) t /= 2;
+  int t = 8;
+  while (t > 2 && cb * (2 * (size_t)t * nz + nz) > 160 * 1024) t /= 2;
   return t;
 }
 
@@ -480,7 +486,7 @@ void choose_rhs_tiles(ppe_plan_t P) {
   int tj = 4;
   while (tj > 1 && rhs_smem(nx, tj) > 110 * 1024) tj /= 2;
   P->tj = tj;
-  P->kc = P->g.nz < 16 ? P->g.nz : 16;
+  P->kc = P->g.nz < 8 ? P->g.nz : 8;
 }
 
 }  // namespace
@@ -563,12 +569,13 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->gd.fd_nyp1 = make_fastdiv((uint32_t)(g->ny + 1));
   const double dy = g->ly / g->ny;
   P->a_y = 1.0 / (dy * dy);
-  P->rp_half = radix_plan(g->nx / 2);
-  P->rp_z = radix_plan(g->nz);
+  const int maxr = P->fp32 ? 16 : 8;  // radix 16 in FP64 would need 128+ registers per butterfly
+  P->rp_half = radix_plan(g->nx / 2, maxr);
+  P->rp_z = radix_plan(g->nz, maxr);
   P->lpb = choose_lpb(g->nx);
   P->tkx = choose_tkx(g->nz, P->fp32);
   P->tky = choose_tkx(g->ny, P->fp32);
-  P->rp_y = radix_plan(g->ny);
+  P->rp_y = radix_plan(g->ny, maxr);
   P->cplx_bytes = P->fp32 ? 8 : 16;
 
   ppe_status s = PPE_OK;

@@ -22,6 +22,7 @@ struct StencilConst {
   df idx, idy, idz;
   df gx, gy, gz;   // (dt/rho_0) / dx, ...
   df lx, ly, lz;   // 1/dx^2, 1/dy^2, 1/dz^2
+  df cx, cy, cz;   // (rho_0/dt) dx, (rho_0/dt) dy, (rho_0/dt) dz
 };
 
 // Device-resident scalars of one plan.  Non-negative doubles are kept as their

@@ -37,14 +37,34 @@ __device__ __forceinline__ StencilConst make_const(const GridDev& g, double rho0
   K.lx = d2df(g.idx * g.idx);
   K.ly = d2df(g.idy * g.idy);
   K.lz = d2df(g.idz * g.idz);
+  K.cx = d2df(rho0 / dt / g.idx);
+  K.cy = d2df(rho0 / dt / g.idy);
+  K.cz = d2df(rho0 / dt / g.idz);
   return K;
 }
 
 // beta_f = 1 - rho_0 / rho_f for the face between cells with densities a, b
+// (unnormalised pair; see the lazy operations in dfloat.cuh)
 __device__ __forceinline__ df beta_df(df a, df b, const StencilConst& K, int rule) {
   const df one = {1.0f, 0.0f};
-  if (rule == 0) return df_sub(one, df_mul(K.r02, df_recip(df_add(a, b))));      // 1 - 2 rho_0/(a+b)
-  return df_sub(one, df_mul(K.r0h, df_add(df_recip(a), df_recip(b))));           // 1 - (rho_0/2)(1/a+1/b)
+  if (rule == 0) return df_subz(one, df_mulz(K.r02, df_recipz(df_addz(a, b))));   // 1 - 2 rho_0/(a+b)
+  return df_subz(one, df_mulz(K.r0h, df_addz(df_recipz(a), df_recipz(b))));        // 1 - (rho_0/2)(1/a+1/b)
+}
+
+// Split flux of one face without the 1/h factor, Q~ = beta_f (p_hat_R - p_hat_L)
+// + (rho_0/dt) h u*_f, and the explicitly split velocity
+// u_pre = u*_f + (dt/rho_0)(1/h) beta_f (p_hat_R - p_hat_L); h the spacing of
+// the face's direction, ch = (rho_0/dt) h, gh = (dt/rho_0)/h.
+struct FaceOut {
+  df q, upre;
+};
+__device__ __forceinline__ FaceOut face_q(df rl, df rh, df pl, df ph, df us, df ch, df gh, const StencilConst& K,
+                                          int rule) {
+  const df bg = df_mulz(beta_df(rl, rh, K, rule), df_subz(ph, pl));
+  FaceOut o;
+  o.q = df_norm(df_addz(bg, df_mulz(ch, us)));
+  o.upre = df_norm(df_addz(us, df_mulz(gh, bg)));
+  return o;
 }
 
 __device__ __forceinline__ df phat_df(const double* pn, const double* pnm1, size_t c) {
@@ -69,21 +89,6 @@ __device__ __forceinline__ Nbr neighbours(const GridDev& g, int i, int j, int k)
   n.zp = ((size_t)kp * ny + j) * nx + i;
   n.zm = ((size_t)km * ny + j) * nx + i;
   return n;
-}
-
-// r = f - L p at cell (i, j, k), f and p as pairs; lc = (1/dx^2, 1/dy^2, 1/dz^2)
-__device__ __forceinline__ df resid_df(const GridDev& g, const df* __restrict__ f, const df* __restrict__ p,
-                                       const df lc[3], int i, int j, int k) {
-  const Nbr n = neighbours(g, i, j, k);
-  const size_t nx = (size_t)g.nx;
-  const df p0 = p[n.c];
-  const df lx = df_sub(df_sub(p[n.xp], p0), df_sub(p0, p[n.xm]));
-  const df lz = df_sub(df_sub(p[n.zp], p0), df_sub(p0, p[n.zm]));
-  df ly = {0.0f, 0.0f};
-  if (j + 1 < g.ny) ly = df_sub(p[n.c + nx], p0);
-  if (j > 0) ly = df_sub(ly, df_sub(p0, p[n.c - nx]));
-  const df lap = df_add(df_add(df_mul(lx, lc[0]), df_mul(ly, lc[1])), df_mul(lz, lc[2]));
-  return df_sub(f[n.c], lap);
 }
 
 __device__ __forceinline__ void block_max_to(unsigned long long* slot, float v) {
