@@ -15,12 +15,13 @@
 // (dfloat.cuh) and every face and cell value is formed in pair arithmetic.
 //
 // Blocking: a CTA owns `tj` consecutive y-lines for a chunk of `kc` z-planes and
-// marches upward in z.  Shared memory holds, for the current plane and the one
-// above, p_hat and rho of the tj lines plus one halo line on each side (a
-// 2-plane ring), and the face values Q of the x faces, y faces and the two z
-// faces of the current plane.  Each input value is converted once per CTA
-// (plus halo), each face is evaluated once.  f is written as float pairs (the
-// forward x transform reads it back, k_xfwd) and/or as FP64.
+// marches upward in z.  Each thread owns fixed (i, j) columns of the tile and
+// keeps in registers the next plane's p_hat and rho and the value of the lower
+// z face of its cells; shared memory holds the current plane's p_hat and rho
+// (the tj lines plus one halo line on each side) and the x- and y-face values.
+// Each input value is converted once per CTA (plus halo lines), each face is
+// evaluated once.  f is written as float pairs (the forward x transform reads
+// it back, k_xfwd) and/or as FP64.
 #include "dfloat.cuh"
 #include "ppe_internal.h"
 #include "stencil.cuh"
@@ -35,223 +36,218 @@ struct RhsOut {
   df* wpre;      //           w_pre on z faces  [nz][ny][nx]
 };
 
-__global__ void __launch_bounds__(256) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int tj,
-                                                   int kc) {
+constexpr int kRhsThreads = 256;
+constexpr int kRhsMaxCols = 8;  // columns per thread: tj * nx <= 2048
+
+// CPT: columns per thread (tj * nx <= CPT * kRhsThreads)
+template <int CPT>
+__global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out,
+                                                           int tj, int kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int ntile = (ny + tj - 1) / tj;
   const int jt = blockIdx.x % ntile, kci = blockIdx.x / ntile;
   const int j0 = jt * tj, k0 = kci * kc;
   const int steps = min(kc, nz - k0);
-  const int nl = tj + 2;  // ring lines per plane
+  const int nl = tj + 2;  // lines of the current plane held in shared memory (with halos)
   const int rule = in.face_rule;
 
-  // shared layout
-  df* P = reinterpret_cast<df*>(smem_raw);          // [2][nl][nx]
-  df* R = P + 2 * nl * nx;                          // [2][nl][nx]
-  df* QX = R + 2 * nl * nx;                         // [tj][nx]
-  df* QY = QX + tj * nx;                            // [tj+1][nx]
-  df* QZ = QY + (tj + 1) * nx;                      // [2][tj][nx]
+  // shared: current plane p_hat and rho (nl lines), x-face and y-face values
+  df* P = reinterpret_cast<df*>(smem_raw);  // [nl][nx]
+  df* R = P + nl * nx;                      // [nl][nx]
+  df* QX = R + nl * nx;                     // [tj][nx]
+  df* QY = QX + tj * nx;                    // [tj+1][nx]
 
   const StencilConst K = sc->K;  // formed once per call by k_make_const
   // 32-bit element offsets (grids up to 1024^3 stay below 2^32)
   const uint32_t plane = (uint32_t)ny * (uint32_t)nx;
   const uint32_t vplane = (uint32_t)(ny + 1) * (uint32_t)nx;
+  const int ncol = tj * nx;
 
-  // Loops below take their items in chunks of U per thread and issue all of a
-  // chunk's global loads before the first use, so that a CTA waits about once
-  // per phase instead of once per item.
-  constexpr int UR = 6, UF = 4;
-  const int nthr = blockDim.x;
+  // this thread's columns (i, jj), fixed for the whole march
+  int ci[CPT], cj[CPT];
+  bool cv[CPT];
+#pragma unroll
+  for (int u = 0; u < CPT; ++u) {
+    const int c = threadIdx.x + u * kRhsThreads;
+    cj[u] = (int)fdiv((uint32_t)c, g.fd_nx);
+    ci[u] = c - cj[u] * nx;
+    cv[u] = c < ncol && j0 + cj[u] < ny;
+  }
+  // registers: p_hat, rho of the plane above the current one; Q of the lower z face
+  df P1[CPT], R1[CPT], QZ[CPT];
 
-  // ring slot s <- plane kk (periodic), lines j0-1 .. j0+tj
-  auto load_plane = [&](int slot, int kk) {
-    kk = (kk % nz + nz) % nz;
-    df* Ps = P + slot * nl * nx;
-    df* Rs = R + slot * nl * nx;
-    const int total = nl * nx;
-    for (int b0 = 0; b0 < total; b0 += UR * nthr) {
-      double vn[UR], vm[UR], vr[UR];
+  auto cell = [&](int kk, int j, int i) -> uint32_t { return (uint32_t)kk * plane + (uint32_t)(j * nx + i); };
+  auto wrapk = [&](int kk) { return (kk % nz + nz) % nz; };
+
+  // own columns of plane kk into (pv, rv)
+  auto load_cols = [&](int kk, df* pv, df* rv) {
+    kk = wrapk(kk);
+    double a[CPT], b[CPT], r[CPT];
 #pragma unroll
-      for (int u = 0; u < UR; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        const int l = (int)fdiv(idx, g.fd_nx), i = idx - l * nx;
-        const int j = j0 - 1 + l;
-        vn[u] = 0.0;
-        vm[u] = 0.0;
-        vr[u] = 1.0;
-        if (idx < total && j >= 0 && j < ny) {
-          const uint32_t c = (uint32_t)kk * plane + (uint32_t)(j * nx + i);
-          vn[u] = __ldg(in.pn + c);
-          vm[u] = __ldg(in.pnm1 + c);
-          vr[u] = __ldg(in.rho + c);
-        }
+    for (int u = 0; u < CPT; ++u) {
+      a[u] = 0.0; b[u] = 0.0; r[u] = 1.0;
+      if (cv[u]) {
+        const uint32_t c = cell(kk, j0 + cj[u], ci[u]);
+        a[u] = __ldg(in.pn + c);
+        b[u] = __ldg(in.pnm1 + c);
+        r[u] = __ldg(in.rho + c);
       }
+    }
 #pragma unroll
-      for (int u = 0; u < UR; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        if (idx < total) {
-          Ps[idx] = df_sub(df_ldexp2(d2df(vn[u])), d2df(vm[u]));
-          Rs[idx] = d2df(vr[u]);
-        }
+    for (int u = 0; u < CPT; ++u) {
+      pv[u] = df_sub(df_ldexp2(d2df(a[u])), d2df(b[u]));  // p_hat = 2 p^n - p^{n-1}
+      rv[u] = d2df(r[u]);
+    }
+  };
+  // halo lines j0-1 and j0+tj of plane kk into shared lines 0 and nl-1
+  auto load_halo = [&](int kk) {
+    kk = wrapk(kk);
+    for (int idx = threadIdx.x; idx < 2 * nx; idx += kRhsThreads) {
+      const int h = idx >= nx, i = idx - h * nx;
+      const int j = h ? j0 + tj : j0 - 1;
+      const int l = h ? nl - 1 : 0;
+      df pv = {0.0f, 0.0f}, rv = {1.0f, 0.0f};
+      if (j >= 0 && j < ny) {
+        const uint32_t c = cell(kk, j, i);
+        pv = df_sub(df_ldexp2(d2df(__ldg(in.pn + c))), d2df(__ldg(in.pnm1 + c)));
+        rv = d2df(__ldg(in.rho + c));
       }
+      P[l * nx + i] = pv;
+      R[l * nx + i] = rv;
+    }
+  };
+  // z face kf (between planes kf-1 and kf) of own columns from (pl, rl) below and (ph, rh) above
+  auto z_face = [&](int kf, const df* pl, const df* rl, const df* ph, const df* rh, bool owned, df* q) {
+    kf = wrapk(kf);
+    double ws[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) ws[u] = cv[u] ? __ldg(in.w + cell(kf, j0 + cj[u], ci[u])) : 0.0;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      q[u] = {0.0f, 0.0f};
+      if (!cv[u]) continue;
+      const FaceOut fo = face_q(rl[u], rh[u], pl[u], ph[u], d2df(ws[u]), K.cz, K.gz, K, rule);
+      q[u] = fo.q;
+      if (owned && out.wpre) out.wpre[cell(kf, j0 + cj[u], ci[u])] = fo.upre;
     }
   };
 
-  // z face between plane (slot lo) and (slot hi): lines jj < tj; face index
-  // kf = the upper plane's index; store Q in QZ[zs]; write w_pre if owned
-  auto z_faces = [&](int slot_lo, int slot_hi, int kf, int zs, bool owned) {
-    kf = (kf % nz + nz) % nz;
-    const df* Pl = P + slot_lo * nl * nx;
-    const df* Ph = P + slot_hi * nl * nx;
-    const df* Rl = R + slot_lo * nl * nx;
-    const df* Rh = R + slot_hi * nl * nx;
-    const int total = tj * nx;
-    for (int b0 = 0; b0 < total; b0 += UF * nthr) {
-      double ws[UF];
+  // prologue: plane k0 in shared memory (own lines from registers, halos
+  // loaded), face k0 from planes k0-1 and k0, plane k0+1 in registers
+  {
+    df P0[CPT], R0[CPT];
+    load_cols(k0 - 1, P1, R1);
+    load_cols(k0, P0, R0);
+    z_face(k0, P1, R1, P0, R0, true, QZ);
 #pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        ws[u] = 0.0;
-        if (idx < total && j0 + jj < ny) ws[u] = __ldg(in.w + ((uint32_t)kf * plane + (uint32_t)((j0 + jj) * nx + i)));
+    for (int u = 0; u < CPT; ++u)
+      if (threadIdx.x + u * kRhsThreads < ncol) {
+        P[(cj[u] + 1) * nx + ci[u]] = P0[u];
+        R[(cj[u] + 1) * nx + ci[u]] = R0[u];
       }
-#pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        if (idx >= total) continue;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        const int j = j0 + jj;
-        df q = {0.0f, 0.0f};
-        if (j < ny) {
-          const int r = (jj + 1) * nx + i;
-          const FaceOut fo = face_q(Rl[r], Rh[r], Pl[r], Ph[r], d2df(ws[u]), K.cz, K.gz, K, rule);
-          q = fo.q;
-          if (owned && out.wpre) out.wpre[(uint32_t)kf * plane + (uint32_t)(j * nx + i)] = fo.upre;
-        }
-        QZ[zs * tj * nx + idx] = q;
-      }
-    }
-  };
-
-  // prologue: plane k0-1 in slot 1, plane k0 in slot 0, face k0 -> QZ[0]
-  load_plane(1, k0 - 1);
-  load_plane(0, k0);
-  __syncthreads();
-  z_faces(1, 0, k0, 0, true);
-  __syncthreads();
-  load_plane(1, k0 + 1);
+    load_halo(k0);
+    load_cols(k0 + 1, P1, R1);
+  }
   __syncthreads();
 
   float vmax = 0.0f;
   for (int st = 0; st < steps; ++st) {
     const int k = k0 + st;
-    const int a = st & 1, b = a ^ 1;  // slot of plane k, plane k+1
-    const int zdn = st & 1, zup = zdn ^ 1;
-    const df* Pa = P + a * nl * nx;
-    const df* Ra = R + a * nl * nx;
-    // ---- phase A: x faces and y faces of plane k, z face k+1
-    for (int b0 = 0; b0 < tj * nx; b0 += UF * nthr) {
-      double us_[UF];
+    // ---- phase A: faces of plane k (x, y from shared; z face k+1 from registers)
+    double us_[CPT], ss_[CPT];
 #pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        us_[u] = 0.0;
-        if (idx < tj * nx && j0 + jj < ny) us_[u] = __ldg(in.u + ((uint32_t)k * plane + (uint32_t)((j0 + jj) * nx + i)));
+    for (int u = 0; u < CPT; ++u) {
+      us_[u] = cv[u] ? __ldg(in.u + cell(k, j0 + cj[u], ci[u])) : 0.0;
+      ss_[u] = cv[u] ? __ldg(in.S + cell(k, j0 + cj[u], ci[u])) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      if (threadIdx.x + u * kRhsThreads >= ncol) continue;
+      df q = {0.0f, 0.0f};
+      if (cv[u]) {
+        const int r = (cj[u] + 1) * nx;
+        const int i = ci[u], im = (i == 0) ? nx - 1 : i - 1;
+        const FaceOut fo = face_q(R[r + im], R[r + i], P[r + im], P[r + i], d2df(us_[u]), K.cx, K.gx, K, rule);
+        q = fo.q;
+        if (out.upre) out.upre[cell(k, j0 + cj[u], i)] = fo.upre;
       }
-#pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        if (idx >= tj * nx) continue;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        const int j = j0 + jj;
-        df q = {0.0f, 0.0f};
-        if (j < ny) {
-          const int r = (jj + 1) * nx;
-          const int im = (i == 0) ? nx - 1 : i - 1;
-          const FaceOut fo = face_q(Ra[r + im], Ra[r + i], Pa[r + im], Pa[r + i], d2df(us_[u]), K.cx, K.gx, K, rule);
+      QX[cj[u] * nx + ci[u]] = q;
+    }
+    for (int idx = threadIdx.x; idx < (tj + 1) * nx; idx += kRhsThreads) {
+      const int jf = (int)fdiv((uint32_t)idx, g.fd_nx), i = idx - jf * nx;
+      const int j = j0 + jf;  // face between cells j-1 and j
+      df q = {0.0f, 0.0f};
+      if (j <= ny) {
+        const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
+        const df vs = d2df(__ldg(in.v + cvv));
+        const bool own = (jf < tj) || (j == ny);
+        if (j == 0 || j == ny) {
+          q = df_norm(df_mulz(K.cy, vs));
+          if (own && out.vpre) out.vpre[cvv] = vs;
+        } else {
+          const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
+          const FaceOut fo = face_q(R[rl], R[rh], P[rl], P[rh], vs, K.cy, K.gy, K, rule);
           q = fo.q;
-          if (out.upre) out.upre[(uint32_t)k * plane + (uint32_t)(j * nx + i)] = fo.upre;
+          if (own && out.vpre) out.vpre[cvv] = fo.upre;
         }
-        QX[idx] = q;
       }
+      QY[idx] = q;
     }
-    for (int b0 = 0; b0 < (tj + 1) * nx; b0 += UF * nthr) {
-      double vs_[UF];
+    df QZup[CPT];
+    {
+      df Pk[CPT], Rk[CPT];
 #pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        const int jf = (int)fdiv(idx, g.fd_nx), i = idx - jf * nx;
-        vs_[u] = 0.0;
-        if (idx < (tj + 1) * nx && j0 + jf <= ny) vs_[u] = __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)((j0 + jf) * nx + i)));
+      for (int u = 0; u < CPT; ++u) {
+        Pk[u] = cv[u] ? P[(cj[u] + 1) * nx + ci[u]] : df{0.0f, 0.0f};
+        Rk[u] = cv[u] ? R[(cj[u] + 1) * nx + ci[u]] : df{1.0f, 0.0f};
       }
-#pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        if (idx >= (tj + 1) * nx) continue;
-        const int jf = (int)fdiv(idx, g.fd_nx), i = idx - jf * nx;
-        const int j = j0 + jf;  // face between cells j-1 and j
-        df q = {0.0f, 0.0f};
-        if (j <= ny) {
-          const uint32_t cv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
-          const df vs = d2df(vs_[u]);
-          const bool own = (jf < tj) || (j == ny);
-          if (j == 0 || j == ny) {
-            q = df_norm(df_mulz(K.cy, vs));
-            if (own && out.vpre) out.vpre[cv] = vs;
-          } else {
-            const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
-            const FaceOut fo = face_q(Ra[rl], Ra[rh], Pa[rl], Pa[rh], vs, K.cy, K.gy, K, rule);
-            q = fo.q;
-            if (own && out.vpre) out.vpre[cv] = fo.upre;
-          }
-        }
-        QY[idx] = q;
-      }
+      z_face(k + 1, Pk, Rk, P1, R1, k + 1 < k0 + steps, QZup);
     }
-    z_faces(a, b, k + 1, zup, k + 1 < k0 + steps);
     __syncthreads();
     // ---- phase B: cells of plane k
-    for (int b0 = 0; b0 < tj * nx; b0 += UF * nthr) {
-      double ss_[UF];
 #pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        ss_[u] = 0.0;
-        if (idx < tj * nx && j0 + jj < ny) ss_[u] = __ldg(in.S + ((uint32_t)k * plane + (uint32_t)((j0 + jj) * nx + i)));
-      }
-#pragma unroll
-      for (int u = 0; u < UF; ++u) {
-        const int idx = b0 + u * nthr + threadIdx.x;
-        if (idx >= tj * nx) continue;
-        const int jj = (int)fdiv(idx, g.fd_nx), i = idx - jj * nx;
-        const int j = j0 + jj;
-        if (j < ny) {
-          const int ip = (i + 1 == nx) ? 0 : i + 1;
-          // f = sum over directions of (Q~_+ - Q~_-) / h^2 - (rho_0/dt) S
-          const df dxq = df_mulz(df_subz(QX[jj * nx + ip], QX[idx]), K.lx);
-          const df dyq = df_mulz(df_subz(QY[(jj + 1) * nx + i], QY[idx]), K.ly);
-          const df dzq = df_mulz(df_subz(QZ[zup * tj * nx + idx], QZ[zdn * tj * nx + idx]), K.lz);
-          const uint32_t c = (uint32_t)k * plane + (uint32_t)(j * nx + i);
-          const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, d2df(ss_[u]))));
-          if (out.fdf) out.fdf[c] = f;
-          if (out.f64) out.f64[c] = df2d(f);
-          vmax = fmaxf(vmax, fabsf(f.hi));
-        }
-      }
+    for (int u = 0; u < CPT; ++u) {
+      if (!cv[u]) continue;
+      const int i = ci[u], jj = cj[u];
+      const int ip = (i + 1 == nx) ? 0 : i + 1;
+      // f = sum over directions of (Q~_+ - Q~_-) / h^2 - (rho_0/dt) S
+      const df dxq = df_mulz(df_subz(QX[jj * nx + ip], QX[jj * nx + i]), K.lx);
+      const df dyq = df_mulz(df_subz(QY[(jj + 1) * nx + i], QY[jj * nx + i]), K.ly);
+      const df dzq = df_mulz(df_subz(QZup[u], QZ[u]), K.lz);
+      const uint32_t c = cell(k, j0 + jj, i);
+      const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, d2df(ss_[u]))));
+      if (out.fdf) out.fdf[c] = f;
+      if (out.f64) out.f64[c] = df2d(f);
+      vmax = fmaxf(vmax, fabsf(f.hi));
+      QZ[u] = QZup[u];
     }
-    // ---- slot a (plane k) is free: load plane k+2 for the next step
-    if (st + 1 < steps) load_plane(a, k + 2);
-    __syncthreads();
+    if (st + 1 < steps) {
+      __syncthreads();
+      // ---- phase C: plane k+1 becomes current; plane k+2 into registers
+#pragma unroll
+      for (int u = 0; u < CPT; ++u)
+        if (threadIdx.x + u * kRhsThreads < ncol) {
+          P[(cj[u] + 1) * nx + ci[u]] = P1[u];
+          R[(cj[u] + 1) * nx + ci[u]] = R1[u];
+        }
+      load_halo(k + 1);
+      load_cols(k + 2, P1, R1);
+      __syncthreads();
+    }
   }
   block_max_to(&sc->fmax_bits, vmax);
 }
 
 size_t rhs_smem(int nx, int tj) {
   const size_t nl = tj + 2;
-  return sizeof(df) * (4 * nl * nx + (size_t)tj * nx + (size_t)(tj + 1) * nx + 2 * (size_t)tj * nx);
+  return sizeof(df) * (2 * nl * nx + (size_t)tj * nx + (size_t)(tj + 1) * nx);
+}
+
+int rhs_max_lines(int nx) {
+  int tj = 8;
+  while (tj > 1 && tj * nx > kRhsThreads * kRhsMaxCols) tj /= 2;
+  return tj;
 }
 
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
@@ -264,12 +260,26 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
   o.wpre = wpre;
   const int ntile = (g.ny + tj - 1) / tj;
   const int nchunk = (g.nz + kc - 1) / kc;
-  k_rhs_march<<<ntile * nchunk, 256, rhs_smem(g.nx, tj), st>>>(g, in, sc, o, tj, kc);
+  const int ncol = tj * g.nx;
+  const size_t sm = rhs_smem(g.nx, tj);
+  const int grid = ntile * nchunk;
+  if (ncol <= kRhsThreads)
+    k_rhs_march<1><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
+  else if (ncol <= 2 * kRhsThreads)
+    k_rhs_march<2><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
+  else if (ncol <= 4 * kRhsThreads)
+    k_rhs_march<4><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
+  else
+    k_rhs_march<8><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
   return cudaGetLastError();
 }
 
 cudaError_t set_rhs_smem_limit() {
-  return cudaFuncSetAttribute(k_rhs_march, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_rhs_march<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 }  // namespace ppe

@@ -74,6 +74,7 @@ enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
                        df* vpre, df* wpre, int tj, int kc, cudaStream_t st);
 size_t rhs_smem(int nx, int tj);
+int rhs_max_lines(int nx);  // tj * nx may not exceed the columns the threads of a CTA hold
 cudaError_t set_rhs_smem_limit();
 
 // ---- launchers (k_spectral.cu) ----
