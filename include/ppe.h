@@ -148,6 +148,23 @@ ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
  * plan's stream before returning. */
 ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
 
+/* Batched projections (many grids of any sizes in one launch).  Each plan
+ * (distinct; a plan may appear once per batch) is paired with its fields.
+ * ppe_batch_create captures the projections once into a CUDA graph whose
+ * independent branches run concurrently; every ppe_batch_launch then replays
+ * the whole batch with one graph launch on `stream`.  The field pointers are
+ * baked into the graph: launch again only with the same buffers (their
+ * contents may change).  Per-plan results (ppe_get_info) are valid after the
+ * caller has synchronised `stream`.  PPE_ERR_INVALID_ARG for n < 1, NULL
+ * arrays, a repeated plan or invalid fields; PPE_ERR_CUDA if capture fails. */
+typedef struct ppe_batch_s* ppe_batch_t;
+ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                            void* stream);
+ppe_status ppe_batch_launch(ppe_batch_t batch);
+void ppe_batch_destroy(ppe_batch_t batch);
+/* One-shot form: create, launch, synchronise `stream`, destroy. */
+ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields* fields, void* stream);
+
 /* Synchronise the plan's stream and read the device-side results. */
 ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
 

@@ -373,18 +373,70 @@ ppe_status refine_body(ppe_plan_t P, int mode, cudaGraphConditionalHandle h, int
   return PPE_OK;
 }
 
+// Appends a refinement sequence to the graph that P->stream is capturing:
+// [probe]; WHILE(cond) { body }, the condition set on the device by the test
+// kernel.  Used to build the per-plan refinement graphs and, when a caller
+// captures ppe_project (e.g. ppe_batch_create), inline in the caller's graph.
+ppe_status capture_refine(ppe_plan_t P, int mode) {
+  const int saved_prof = P->prof_on;
+  P->prof_on = 0;
+  cudaStream_t cs = P->stream;
+  cudaStream_t bs = nullptr;
+  ppe_status st = PPE_OK;
+  auto done = [&](ppe_status s) {
+    P->stream = cs;
+    P->prof_on = saved_prof;
+    if (bs) cudaStreamDestroy(bs);
+    if (s != PPE_OK) cudaGetLastError();
+    return s;
+  };
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess ||
+      cst != cudaStreamCaptureStatusActive)
+    return done(PPE_ERR_CUDA);
+  cudaGraphConditionalHandle h;
+  // REF_PROJECT runs its body at least once: the condition starts at 1
+  if (cudaGraphConditionalHandleCreate(&h, cg, mode == REF_PROJECT ? 1u : 0u, cudaGraphCondAssignDefault) !=
+      cudaSuccess)
+    return done(PPE_ERR_CUDA);
+  if (mode == REF_SOLVE) {
+    if ((st = refine_probe(P, h, 1)) != PPE_OK) return done(st);
+    if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess)
+      return done(PPE_ERR_CUDA);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond = nullptr;
+  if (cudaGraphAddNode(&cond, cg, deps, nullptr, ndeps, &cp) != cudaSuccess) return done(PPE_ERR_CUDA);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return done(PPE_ERR_CUDA);
+  // the body is captured from a second stream into the conditional's graph
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return done(PPE_ERR_CUDA);
+  if (cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return done(PPE_ERR_CUDA);
+  P->stream = bs;
+  st = refine_body(P, mode, h, 1);
+  P->stream = cs;
+  cudaGraph_t outb = nullptr;
+  if (cudaStreamEndCapture(bs, &outb) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+  return done(st);
+}
+
 // Builds a refinement graph once per plan (it touches plan-owned buffers and
-// the device scalar block only): [probe]; WHILE(cond) { body }.
+// the device scalar block only).
 ppe_status build_refine_graph(ppe_plan_t P, int mode, cudaGraphExec_t* exec) {
   cudaStream_t saved = P->stream;
-  const int saved_prof = P->prof_on;
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
-  cudaGraphConditionalHandle h;
-  ppe_status st = PPE_OK;
   auto fail = [&](ppe_status s) {
     P->stream = saved;
-    P->prof_on = saved_prof;
     if (g) cudaGraphDestroy(g);
     if (cs) cudaStreamDestroy(cs);
     cudaGetLastError();
@@ -392,47 +444,15 @@ ppe_status build_refine_graph(ppe_plan_t P, int mode, cudaGraphExec_t* exec) {
   };
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(PPE_ERR_CUDA);
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
-  // REF_PROJECT runs its body at least once: the condition starts at 1
-  if (cudaGraphConditionalHandleCreate(&h, g, mode == REF_PROJECT ? 1u : 0u, cudaGraphCondAssignDefault) !=
-      cudaSuccess)
-    return fail(PPE_ERR_CUDA);
-  P->stream = cs;
-  P->prof_on = 0;
   if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(PPE_ERR_CUDA);
-  if (mode == REF_SOLVE) st = refine_probe(P, h, 1);
-  cudaStreamCaptureStatus cst;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  cudaGraph_t cg = nullptr;
-  if (st == PPE_OK && cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess)
-    st = PPE_ERR_CUDA;
-  cudaGraphNode_t cond = nullptr;
-  cudaGraph_t body = nullptr;
-  if (st == PPE_OK) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    if (cudaGraphAddNode(&cond, cg, deps, nullptr, ndeps, &cp) != cudaSuccess) st = PPE_ERR_CUDA;
-    else body = cp.conditional.phGraph_out[0];
-  }
-  if (st == PPE_OK &&
-      cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
-    st = PPE_ERR_CUDA;
+  P->stream = cs;
+  ppe_status st = capture_refine(P, mode);
+  P->stream = saved;
   cudaGraph_t outg = nullptr;
   if (cudaStreamEndCapture(cs, &outg) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
   if (st != PPE_OK) return fail(st);
-  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return fail(PPE_ERR_CUDA);
-  st = refine_body(P, mode, h, 1);
-  cudaGraph_t outb = nullptr;
-  if (cudaStreamEndCapture(cs, &outb) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
-  if (st != PPE_OK) return fail(st);
   if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
-  P->stream = saved;
-  P->prof_on = saved_prof;
   cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
   return PPE_OK;
@@ -459,6 +479,9 @@ ppe_status refine(ppe_plan_t P, int mode) {
     PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, 0, 1, none, 0, P->stream));
     return PPE_OK;
   }
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  PPE_TRY(cudaStreamIsCapturing(P->stream, &cst));
+  if (cst == cudaStreamCaptureStatusActive) return capture_refine(P, mode);  // the caller builds a graph
   if (!P->prof_on) {
     PPE_TRY(cudaGraphLaunch(mode == REF_SOLVE ? P->refine_exec : P->project_exec, P->stream));
     return PPE_OK;
@@ -797,6 +820,102 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
                                                 F->u_out, F->v_out, F->w_out, P->stream));
   }
   return PPE_OK;
+}
+
+struct ppe_batch_s {
+  cudaGraphExec_t exec;
+  cudaStream_t stream;
+  int n;
+};
+
+ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                            void* stream) {
+  if (!out || n < 1 || !plans || !fields) return PPE_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return PPE_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return PPE_ERR_INVALID_ARG;
+  }
+  const int nb = n < 16 ? n : 16;  // branch streams: solves on one stream run in order
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> bs(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaGraph_t g = nullptr;
+  ppe_status st = PPE_OK;
+  bool capturing = false;
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : bs)
+      if (s) cudaStreamDestroy(s);
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+  };
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) st = PPE_ERR_CUDA;
+  for (int b = 0; st == PPE_OK && b < nb; ++b)
+    if (cudaStreamCreateWithFlags(&bs[b], cudaStreamNonBlocking) != cudaSuccess) st = PPE_ERR_CUDA;
+  for (int b = 0; st == PPE_OK && b <= nb; ++b)
+    if (cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming) != cudaSuccess) st = PPE_ERR_CUDA;
+  if (st == PPE_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PPE_ERR_CUDA;
+  capturing = st == PPE_OK;
+  if (st == PPE_OK && cudaEventRecord(ev[nb], cs) != cudaSuccess) st = PPE_ERR_CUDA;
+  for (int b = 0; st == PPE_OK && b < nb; ++b)
+    if (cudaStreamWaitEvent(bs[b], ev[nb], 0) != cudaSuccess) st = PPE_ERR_CUDA;
+  for (int i = 0; st == PPE_OK && i < n; ++i) {
+    ppe_plan_t P = plans[i];
+    cudaStream_t saved = P->stream;
+    P->stream = bs[i % nb];
+    st = ppe_project(P, &fields[i]);
+    P->stream = saved;
+  }
+  for (int b = 0; st == PPE_OK && b < nb; ++b) {
+    if (cudaEventRecord(ev[b], bs[b]) != cudaSuccess || cudaStreamWaitEvent(cs, ev[b], 0) != cudaSuccess)
+      st = PPE_ERR_CUDA;
+  }
+  if (capturing) {
+    cudaGraph_t cg = nullptr;
+    if (cudaStreamEndCapture(cs, &cg) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+    g = cg;
+  }
+  ppe_batch_t B = nullptr;
+  if (st == PPE_OK) {
+    B = new (std::nothrow) ppe_batch_s;
+    if (!B) st = PPE_ERR_OUT_OF_MEMORY;
+  }
+  if (st == PPE_OK && cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) st = PPE_ERR_CUDA;
+  cleanup();
+  if (st != PPE_OK) {
+    delete B;
+    cudaGetLastError();
+    return st;
+  }
+  B->stream = (cudaStream_t)stream;
+  B->n = n;
+  *out = B;
+  return PPE_OK;
+}
+
+ppe_status ppe_batch_launch(ppe_batch_t B) {
+  if (!B) return PPE_ERR_INVALID_ARG;
+  PPE_TRY(cudaGraphLaunch(B->exec, B->stream));
+  return PPE_OK;
+}
+
+void ppe_batch_destroy(ppe_batch_t B) {
+  if (!B) return;
+  cudaGraphExecDestroy(B->exec);
+  delete B;
+}
+
+ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields* fields, void* stream) {
+  ppe_batch_t B = nullptr;
+  ppe_status s = ppe_batch_create(&B, n, plans, fields, stream);
+  if (s != PPE_OK) return s;
+  s = ppe_batch_launch(B);
+  if (s == PPE_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = PPE_ERR_CUDA;
+  ppe_batch_destroy(B);
+  return s;
 }
 
 ppe_status ppe_project_host(ppe_plan_t P, const ppe_fields* H) {

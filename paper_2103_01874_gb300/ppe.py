@@ -82,6 +82,10 @@ SIGNATURES = {
     "ppe_profile": (c_int, [c_void_p, c_int]),
     "ppe_rho0_noalloc": (c_int, [c_void_p, c_size_t, c_void_p, c_void_p]),
     "ppe_get_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
+    "ppe_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(FieldsC), c_void_p]),
+    "ppe_batch_launch": (c_int, [c_void_p]),
+    "ppe_batch_destroy": (None, [c_void_p]),
+    "ppe_project_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(FieldsC), c_void_p]),
     "ppe_set_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
 }
@@ -180,6 +184,47 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+class Batch:
+    """ppe_batch_create / ppe_batch_launch: the projections of many plans (any
+    grid sizes) captured once into one CUDA graph and replayed with one launch.
+    `items` is a list of (plan, dict of tensors u, v, w, S, rho, p_n, p_nm1, p,
+    u_out, v_out, w_out [, f], dt [, rho0])."""
+
+    def __init__(self, items, stream=None):
+        n = len(items)
+        self._keep = items  # tensors must outlive the graph
+        plans = (c_void_p * n)(*[pl._h.value for pl, _ in items])
+        flds = (FieldsC * n)()
+        for i, (pl, d) in enumerate(items):
+            flds[i] = pl._fields(_ptr, d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], d["dt"],
+                                 d["p"], d["u_out"], d["v_out"], d["w_out"], d.get("f"), d.get("rho0", -1.0))
+        h = c_void_p()
+        _check(lib().ppe_batch_create(ctypes.byref(h), n, plans, flds, c_void_p(_stream_handle(stream))),
+               "ppe_batch_create")
+        self._h = h
+        self.n = n
+
+    def launch(self):
+        _check(lib().ppe_batch_launch(self._h), "ppe_batch_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ppe_batch_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Plan:
