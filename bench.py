@@ -323,11 +323,100 @@ def run_gpu(args):
         "gpu_launches_note": "kernels per timed region of the headline form (profiled re-run of the same steps)",
         "profiled_ms_per_step": ms32p / steps,
     }
+    if args.batched:
+        res["batched"] = run_batched(args, dev)
+    if args.served:
+        res["served"] = run_served(args, dev)
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if dist is not None:
         dist.destroy_process_group()
     return res
+
+
+# ---------------------------------------------------------------------------
+# batched (64 uneven grids in one graph launch) and served (Poisson arrivals)
+# ---------------------------------------------------------------------------
+def run_batched(args, dev):
+    """64 grids, each dimension from {32, 48, 64, 96, 128, 192}, single-interface
+    recipe, FP32 solve + FP64 refinement, captured into one CUDA graph; against
+    a loop of plain FP64 projections of the same grids, one after another."""
+    import torch
+
+    from paper_2103_01874_gb300 import fields, ppe
+    shapes = fields.batch_shapes(64, seed=3)
+    items64, items32 = [], []
+    for n, (nx, ny, nz) in enumerate(shapes):
+        fl = fields.make_fields(nx, ny, nz, seed=200 + n, recipe="single", width=2.0)
+        d = {k: torch.from_numpy(v).to(dev) for k, v in fl.arrays().items()}
+        for prec, items in ((ppe.FP32_REFINE, items32), (ppe.FP64, items64)):
+            plan = ppe.Plan(nx, ny, nz, fl.lx, fl.ly, fl.lz, precision=prec)
+            o = dict(d, p=torch.empty(fl.shape, dtype=torch.float64, device=dev), u_out=torch.empty_like(d["u"]),
+                     v_out=torch.empty_like(d["v"]), w_out=torch.empty_like(d["w"]), dt=fl.dt)
+            items.append((plan, o))
+    stream = torch.cuda.current_stream(dev)
+    batch = ppe.Batch(items32, stream=stream)
+    for _ in range(2):
+        batch.launch()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        batch.launch()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / reps
+    worst = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
+
+    def loop64():
+        for pl, o in items64:
+            pl.set_stream(stream)
+            pl.project(o["u"], o["v"], o["w"], o["S"], o["rho"], o["p_n"], o["p_nm1"], o["dt"], o["p"], o["u_out"],
+                       o["v_out"], o["w_out"])
+    loop64()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        loop64()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_loop = e0.elapsed_time(e1) / reps
+    pts = sum(a * b * c for a, b, c in shapes)
+    batch.close()
+    for pl, _ in items32 + items64:
+        pl.close()
+    return {"workload": "64 uneven grids (dims from {32,48,64,96,128,192}), FP32 solve + FP64 refinement to 1e-10, "
+                        "one CUDA graph launch",
+            "solves_per_s": 64 / (ms_batch * 1e-3), "ms_per_batch": ms_batch, "gpts_per_s": pts / (ms_batch * 1e-3) / 1e9,
+            "max_rel_residual": worst, "cells": pts,
+            "fp64_loop": {"solves_per_s": 64 / (ms_loop * 1e-3), "ms_per_batch": ms_loop}}
+
+
+def run_served(args, dev):
+    """Poisson arrivals (mean 200 req/s) of grids from 64^3 to 384x256x384, half
+    FP64 and half FP32 + refinement, admitted under a 150 GB budget."""
+    from paper_2103_01874_gb300 import ppe, serve
+    shapes = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (256, 256, 256), (384, 256, 384)]
+    probs = [0.3, 0.2, 0.2, 0.15, 0.1, 0.05]
+    reqs = serve.poisson_requests(args.served_requests, rate=200.0, shapes=shapes, probs=probs, seed=11,
+                                  fp64=ppe.FP64, fp32=ppe.FP32_REFINE)
+    ex = serve.CudaExecutor(slots=8, device=dev.index)
+    for s in set(r.shape for r in reqs):
+        ex.template(s)  # resident input templates, generated before the clock starts
+    srv = serve.Server(ex, budget_bytes=150 << 30, slots=8)
+    # one plan per size class and precision created (and launched once) before
+    # the clock starts, as a long-running server would have them resident
+    warm = [serve.Request(-1 - i, s, p, 0, 0.0)
+            for i, (s, p) in enumerate((s, p) for s in shapes for p in (ppe.FP64, ppe.FP32_REFINE))]
+    srv.run(warm)
+    stats, _ = srv.run(reqs)
+    srv.close()
+    worst = max((r.rel_residual for r in reqs if r.precision == ppe.FP32_REFINE), default=float("nan"))
+    out = stats.as_dict()
+    out.update(workload="Poisson 200 req/s, grids 64^3..384x256x384, 50% FP64 / 50% FP32+refine, 150 GB budget, "
+                        "8 slots", requests=len(reqs), max_rel_residual_fp32=worst)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -410,6 +499,9 @@ def main():
     ap.add_argument("--forms", default="fp32,fp64", help="fp32 (always) and/or fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-times", dest="kernel_times", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-served", dest="served", action="store_false")
+    ap.add_argument("--served-requests", type=int, default=200)
     args = ap.parse_args()
     set_grid(args.n)
     if args.warmup < 3:

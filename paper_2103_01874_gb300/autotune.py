@@ -1,0 +1,117 @@
+"""Launch-shape autotuner for libppe plans.
+
+A plan's tile sizes (ppe_set_tuning: lines per CTA of the right-hand-side
+kernel and of the x transforms, columns per CTA of the z and y passes, planes
+per marching chunk) change no result bit, only speed.  `autotune` times the
+candidate shapes on the caller's own fields with the plan's per-kernel CUDA
+events (ppe_profile), coordinate by coordinate -- each shape only moves the
+time of its own kernel -- applies the best, and remembers it in a JSON cache
+keyed by grid, precision, face rule and GPU name, so that later plans of the
+same size class start from the tuned shapes (`apply_cached`).
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import ppe
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ppe_gb300", "tuning.json")
+
+# which kernel each field of ppe_tuning drives, and the values tried
+SEARCH = {
+    "rhs_lines": ("k_rhs_march", (1, 2, 4, 8)),
+    "rhs_planes": ("k_rhs_march", (4, 8, 16, 32)),
+    "x_lines": ("k_xinv", (4, 8, 16, 32, 64)),
+    "z_cols": ("k_zfft_fwd", (2, 4, 8, 16)),
+    "y_cols": ("k_ysolve", (2, 4, 8, 16, 32)),
+}
+
+_lock = threading.Lock()
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name()
+    except Exception:  # pragma: no cover
+        return "unknown"
+
+
+def cache_key(plan: "ppe.Plan", gpu: str | None = None) -> str:
+    return (f"{plan.nx}x{plan.ny}x{plan.nz}|prec{plan.precision}|face{plan.opts.face_rule}|"
+            f"{gpu if gpu is not None else _gpu_name()}")
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
+    with _lock:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def apply_cached(plan: "ppe.Plan", path: str = DEFAULT_CACHE, gpu: str | None = None) -> bool:
+    """Apply a cached tuning for this plan's size class; True if one was found."""
+    entry = load_cache(path).get(cache_key(plan, gpu))
+    if not entry:
+        return False
+    try:
+        plan.set_tuning(**entry["tuning"])
+    except ppe.PPEError:
+        return False
+    return True
+
+
+def _kernel_us(plan, run, kernel: str, reps: int) -> float:
+    plan.profile(True)
+    plan.profile_read()
+    run(reps)
+    kt = plan.profile_read()
+    plan.profile(False)
+    if kernel not in kt:
+        return float("inf")
+    launches, ms = kt[kernel]
+    return 1e3 * ms / launches
+
+
+def autotune(plan: "ppe.Plan", run, reps: int = 3, path: str | None = DEFAULT_CACHE,
+             search: dict | None = None) -> dict:
+    """Tune `plan` in place.  `run(k)` must perform k projections with this plan
+    (the caller's fields, so that the timing is that of the real workload).
+    Returns {"tuning": best shapes, "kernel_us": time of each tuned kernel}."""
+    search = SEARCH if search is None else search
+    run(1)  # warm-up and first-use costs
+    best = plan.get_tuning()
+    times = {}
+    for field, (kernel, values) in search.items():
+        scores = []
+        for v in values:
+            trial = dict(best)
+            trial[field] = v
+            try:
+                plan.set_tuning(**trial)
+            except ppe.PPEError:
+                continue  # shape out of range or too much shared memory for this grid
+            scores.append((_kernel_us(plan, run, kernel, reps), v))
+        if scores:
+            t, v = min(scores)
+            best[field] = v
+            times[field] = {"kernel": kernel, "us": t, "tried": {str(b): a for a, b in scores}}
+        plan.set_tuning(**best)
+    result = {"tuning": best, "kernel_us": times}
+    if path:
+        cache = load_cache(path)
+        cache[cache_key(plan)] = result
+        save_cache(cache, path)
+    return result
