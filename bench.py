@@ -142,6 +142,26 @@ def kernel_bytes(kernel: str, fp32: bool) -> float:
     return table.get(kernel, 0.0)
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` at 256^3 from profiles/traffic.json
+    (an ncu capture, scaled by cells when taken on a smaller grid), or None if
+    the file is missing or the kernel's source has changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            doc = json.load(fh)
+        entry = doc["kernels"][kernel]
+        h = hashlib.sha256()
+        for src in entry["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != entry["source_sha256"]:
+            return None
+        return float(entry["bytes_per_launch_256"])
+    except Exception:
+        return None
+
+
 def step_min_bytes(fp32: bool, sweeps: int) -> float:
     """Minimal-pass traffic of one projection: 21F for FP64 (7 inputs read,
     two half-spectrum round trips, 6 fields re-read by the correction, 4
@@ -184,6 +204,7 @@ def run_gpu(args):
             dist.barrier()
 
     def timed(plan, steps, warmup, profile=False):
+        profile = profile or args.host_refine
         for _ in range(warmup):
             plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt,
                          out["p"], out["u"], out["v"], out["w"])
@@ -282,8 +303,10 @@ def run_gpu(args):
                  for k, v in sorted(kt64.items(), key=lambda kv: -kv[1][1])}
     dbytes = kernel_bytes(dname, True) if dname else 0.0
     achieved = dbytes / (avg_ms * 1e-3) / 1e9 if dbytes and avg_ms > 0 else None
+    traffic = measured_traffic(dname) if dname else None
     roof = {"kernel": dname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+            "algorithmic_bytes": dbytes,
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src}
     sweeps = info32.sweeps
     step_bytes = step_min_bytes(True, sweeps)
@@ -502,6 +525,9 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-served", dest="served", action="store_false")
     ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--host-refine", action="store_true",
+                    help="drive every timed step with per-kernel events (refinement loop from the host), so that a "
+                         "profiler sees each kernel as its own launch")
     args = ap.parse_args()
     set_grid(args.n)
     if args.warmup < 3:
