@@ -41,7 +41,7 @@ constexpr int kRhsMaxCols = 8;  // columns per thread: tj * nx <= 2048
 
 // CPT: columns per thread (tj * nx <= CPT * kRhsThreads)
 template <int CPT>
-__global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out,
+__global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 1)) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out,
                                                            int tj, int kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -133,6 +133,18 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn 
     }
   };
 
+  // raw next-step loads, issued a phase ahead of their use
+  double us_[CPT], ss_[CPT], ws_[CPT];
+  auto load_step = [&](int k) {  // u* and S of plane k, w* of face k+1, own columns
+    const int kw = wrapk(k + 1);
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      us_[u] = cv[u] ? __ldg(in.u + cell(k, j0 + cj[u], ci[u])) : 0.0;
+      ss_[u] = cv[u] ? __ldg(in.S + cell(k, j0 + cj[u], ci[u])) : 0.0;
+      ws_[u] = cv[u] ? __ldg(in.w + cell(kw, j0 + cj[u], ci[u])) : 0.0;
+    }
+  };
+
   // prologue: plane k0 in shared memory (own lines from registers, halos
   // loaded), face k0 from planes k0-1 and k0, plane k0+1 in registers
   {
@@ -148,19 +160,30 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn 
       }
     load_halo(k0);
     load_cols(k0 + 1, P1, R1);
+    load_step(k0);
   }
   __syncthreads();
 
   float vmax = 0.0f;
   for (int st = 0; st < steps; ++st) {
     const int k = k0 + st;
-    // ---- phase A: faces of plane k (x, y from shared; z face k+1 from registers)
-    double us_[CPT], ss_[CPT];
+    const bool more = st + 1 < steps;
+    // raw p^n, p^{n-1}, rho of plane k+2 (own columns): in flight during A and B
+    double rp[CPT], rm[CPT], rr[CPT];
+    if (more) {
+      const int k2 = wrapk(k + 2);
 #pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-      us_[u] = cv[u] ? __ldg(in.u + cell(k, j0 + cj[u], ci[u])) : 0.0;
-      ss_[u] = cv[u] ? __ldg(in.S + cell(k, j0 + cj[u], ci[u])) : 0.0;
+      for (int u = 0; u < CPT; ++u) {
+        rp[u] = 0.0; rm[u] = 0.0; rr[u] = 1.0;
+        if (cv[u]) {
+          const uint32_t c = cell(k2, j0 + cj[u], ci[u]);
+          rp[u] = __ldg(in.pn + c);
+          rm[u] = __ldg(in.pnm1 + c);
+          rr[u] = __ldg(in.rho + c);
+        }
+      }
     }
+    // ---- phase A: faces of plane k (x, y from shared; z face k+1 from registers)
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
       if (threadIdx.x + u * kRhsThreads >= ncol) continue;
@@ -174,35 +197,52 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn 
       }
       QX[cj[u] * nx + ci[u]] = q;
     }
-    for (int idx = threadIdx.x; idx < (tj + 1) * nx; idx += kRhsThreads) {
-      const int jf = (int)fdiv((uint32_t)idx, g.fd_nx), i = idx - jf * nx;
-      const int j = j0 + jf;  // face between cells j-1 and j
-      df q = {0.0f, 0.0f};
-      if (j <= ny) {
-        const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
-        const df vs = d2df(__ldg(in.v + cvv));
-        const bool own = (jf < tj) || (j == ny);
-        if (j == 0 || j == ny) {
-          q = df_norm(df_mulz(K.cy, vs));
-          if (own && out.vpre) out.vpre[cvv] = vs;
-        } else {
-          const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
-          const FaceOut fo = face_q(R[rl], R[rh], P[rl], P[rh], vs, K.cy, K.gy, K, rule);
-          q = fo.q;
-          if (own && out.vpre) out.vpre[cvv] = fo.upre;
+    {
+      constexpr int UY = 4;
+      const int ny_faces = (tj + 1) * nx;
+      for (int b0 = 0; b0 < ny_faces; b0 += UY * kRhsThreads) {
+        double vv[UY];
+#pragma unroll
+        for (int u = 0; u < UY; ++u) {
+          const int idx = b0 + u * kRhsThreads + threadIdx.x;
+          const int jf = (int)fdiv((uint32_t)idx, g.fd_nx), i = idx - jf * nx;
+          vv[u] = (idx < ny_faces && j0 + jf <= ny)
+                      ? __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)((j0 + jf) * nx + i))) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < UY; ++u) {
+          const int idx = b0 + u * kRhsThreads + threadIdx.x;
+          if (idx >= ny_faces) continue;
+          const int jf = (int)fdiv((uint32_t)idx, g.fd_nx), i = idx - jf * nx;
+          const int j = j0 + jf;  // face between cells j-1 and j
+          df q = {0.0f, 0.0f};
+          if (j <= ny) {
+            const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
+            const df vs = d2df(vv[u]);
+            const bool own = (jf < tj) || (j == ny);
+            if (j == 0 || j == ny) {
+              q = df_norm(df_mulz(K.cy, vs));
+              if (own && out.vpre) out.vpre[cvv] = vs;
+            } else {
+              const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
+              const FaceOut fo = face_q(R[rl], R[rh], P[rl], P[rh], vs, K.cy, K.gy, K, rule);
+              q = fo.q;
+              if (own && out.vpre) out.vpre[cvv] = fo.upre;
+            }
+          }
+          QY[idx] = q;
         }
       }
-      QY[idx] = q;
     }
     df QZup[CPT];
-    {
-      df Pk[CPT], Rk[CPT];
 #pragma unroll
-      for (int u = 0; u < CPT; ++u) {
-        Pk[u] = cv[u] ? P[(cj[u] + 1) * nx + ci[u]] : df{0.0f, 0.0f};
-        Rk[u] = cv[u] ? R[(cj[u] + 1) * nx + ci[u]] : df{1.0f, 0.0f};
-      }
-      z_face(k + 1, Pk, Rk, P1, R1, k + 1 < k0 + steps, QZup);
+    for (int u = 0; u < CPT; ++u) {
+      QZup[u] = {0.0f, 0.0f};
+      if (!cv[u]) continue;
+      const int r = (cj[u] + 1) * nx + ci[u];
+      const FaceOut fo = face_q(R[r], R1[u], P[r], P1[u], d2df(ws_[u]), K.cz, K.gz, K, rule);
+      QZup[u] = fo.q;
+      if (k + 1 < k0 + steps && out.wpre) out.wpre[cell(wrapk(k + 1), j0 + cj[u], ci[u])] = fo.upre;
     }
     __syncthreads();
     // ---- phase B: cells of plane k
@@ -222,9 +262,10 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn 
       vmax = fmaxf(vmax, fabsf(f.hi));
       QZ[u] = QZup[u];
     }
-    if (st + 1 < steps) {
+    if (more) {
+      load_step(k + 1);  // next step's u*, S, w*: in flight during the rest of this step
       __syncthreads();
-      // ---- phase C: plane k+1 becomes current; plane k+2 into registers
+      // ---- phase C: plane k+1 becomes current; plane k+2 (loaded above) into registers
 #pragma unroll
       for (int u = 0; u < CPT; ++u)
         if (threadIdx.x + u * kRhsThreads < ncol) {
@@ -232,7 +273,11 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_march(GridDev g, StencilIn 
           R[(cj[u] + 1) * nx + ci[u]] = R1[u];
         }
       load_halo(k + 1);
-      load_cols(k + 2, P1, R1);
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) {
+        P1[u] = df_sub(df_ldexp2(d2df(rp[u])), d2df(rm[u]));
+        R1[u] = d2df(rr[u]);
+      }
       __syncthreads();
     }
   }
