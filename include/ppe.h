@@ -88,6 +88,15 @@ typedef struct {
     ppe_face_rule face_rule;
     double refine_tol;  /* FP32_REFINE: stop once ||f - L p||_inf <= tol ||f||_inf (e.g. 1e-10) */
     int max_sweeps;     /* FP32_REFINE: refinement sweeps after the first FP32 solve (<= 16) */
+    double compat_tol;  /* compatibility of the right-hand side with the walls.  The
+                         * Neumann problem L p = f is solvable only if mean(f) = 0, i.e.
+                         * mean(S) equals the mean wall flux (see ppe_info).  The solve
+                         * always drops the mean of f (reported in
+                         * ppe_info.f_mean_removed); with compat_tol > 0, ppe_get_info
+                         * and ppe_project_host also return PPE_ERR_INCOMPATIBLE_RHS
+                         * when |mean(f)| > compat_tol * ||f||_inf.  0: no check.  The
+                         * paper has no such check; it follows from the divergence
+                         * theorem on the periodic/wall box of Sec. 5. */
 } ppe_options;
 
 /* Read back by ppe_get_info after a solve or projection. */
@@ -96,6 +105,18 @@ typedef struct {
     double rel_residual;  /* FP32_REFINE: last ||f - L p||_inf / ||f||_inf measured; -1 for FP64 */
     double f_max;         /* ||f||_inf of the last right-hand side (-1 if not computed) */
     double rho0;          /* rho_0 used by the last ppe_rhs / ppe_project */
+    /* Compatibility of the last assembled right-hand side (NaN if no ppe_rhs /
+     * ppe_project ran since the plan was made; f_mean_removed also after ppe_solve): */
+    double s_mean;          /* mean of S over the cells, from the divergence theorem:
+                             * sum over cells of D u* keeps only the wall faces and
+                             * sum D(beta G p_hat) = 0, so by Eq. (34)
+                             * mean(S) = wall_flux_mean - (dt/rho_0) mean(f) */
+    double s_absmax;        /* max |S| (float precision) */
+    double wall_flux_mean;  /* sum over (i, k) of (v*(ny) - v*(0)) / dy, divided by nx ny nz */
+    double wall_vmax;       /* max |v*| on the wall faces (float precision) */
+    double f_mean_removed;  /* mean of f (summed in pairs), which the solve drops; the
+                             * refinement residual of PPE_FP32_REFINE leaves it out too
+                             * unless it is below 2^-40 ||f||_inf (rounding noise) */
 } ppe_info;
 
 /* All inputs and outputs of one projection (Eqs. (32)-(34)); device pointers. */
@@ -114,7 +135,8 @@ typedef struct {
 /* Create a plan: validate sizes, allocate the workspace with cudaMalloc, build
  * twiddle tables (host FP64, octant-reduced cos/sin) and the tridiagonal
  * elimination tables for every (kx, kz).  `stream` is a cudaStream_t (NULL =
- * legacy default stream).  opt may be NULL (FP64, arithmetic faces). */
+ * legacy default stream).  opt may be NULL (FP64, arithmetic faces, compat_tol
+ * 1e-12). */
 ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, void* stream);
 
 /* Re-bind the plan to another stream (for graph capture or serving slots). */
@@ -145,7 +167,8 @@ ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
 /* ppe_project with HOST input and output arrays (pinned memory recommended):
  * copies the inputs to plan-owned device buffers (allocated on first use),
  * projects, and copies p, u, v, w (and f if non-NULL) back.  Synchronises the
- * plan's stream before returning. */
+ * plan's stream before returning, and returns the device-side status as
+ * ppe_get_info does. */
 ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
 
 /* Batched projections (many grids of any sizes in one launch).  Each plan
@@ -165,7 +188,10 @@ void ppe_batch_destroy(ppe_batch_t batch);
 /* One-shot form: create, launch, synchronise `stream`, destroy. */
 ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields* fields, void* stream);
 
-/* Synchronise the plan's stream and read the device-side results. */
+/* Synchronise the plan's stream and read the device-side results.  Returns
+ * PPE_ERR_NOT_CONVERGED if the refinement stopped above its tolerance, else
+ * PPE_ERR_INCOMPATIBLE_RHS if the compatibility test of ppe_options.compat_tol
+ * failed for the last solve's f (info is filled in both cases), else PPE_OK. */
 ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
 
 /* Free the workspace.  NULL is ignored. */

@@ -128,6 +128,21 @@ def ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC
 # Eq. (34): direct solve of L p = f (the paper's FFT Poisson solver)
 # ----------------------------------------------------------------------------
 
+def compatibility(v, S, lengths):
+    """Solvability of the Neumann problem L p = f (Sec. 5.4, Eq. (34)): the sum of
+    f over the cells must vanish.  Summing D over the cells leaves only the wall
+    faces of y (x and z are periodic), and G vanishes on the walls, so
+    mean(f) = (rho_0/dt) (wall_flux_mean - mean(S)) with
+    wall_flux_mean = sum over (i, k) of (v[:, Ny, :] - v[:, 0, :]) / (dy Nx Ny Nz).
+    Returns the plain definitions: dict(s_mean, s_absmax, wall_flux_mean, wall_vmax)."""
+    nz, ny, nx = S.shape
+    dy = lengths[1] / ny
+    wall = np.concatenate([v[:, 0, :].ravel(), v[:, ny, :].ravel()])
+    return dict(s_mean=float(S.sum() / S.size), s_absmax=float(np.abs(S).max()),
+                wall_flux_mean=float((v[:, ny, :] - v[:, 0, :]).sum() / (dy * S.size)),
+                wall_vmax=float(np.abs(wall).max()))
+
+
 def eigenvalues(shape, lengths):
     """Eigenvalues of L for the Fourier (x, z) x cosine (y) modes, shape
     [Nz][Ny][Nx//2+1] matching rfft in x, full fft in z, DCT-II in y."""

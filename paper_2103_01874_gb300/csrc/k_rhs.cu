@@ -28,6 +28,9 @@
 
 namespace ppe {
 
+constexpr int kRhsThreads = 256;
+constexpr int kRhsMaxCols = 8;  // columns per thread: tj * nx <= 2048
+
 struct RhsOut {
   double* f64;   // optional: f as FP64
   df* fdf;       // optional: f as pairs (kept for the residual)
@@ -36,8 +39,7 @@ struct RhsOut {
   df* wpre;      //           w_pre on z faces  [nz][ny][nx]
 };
 
-constexpr int kRhsThreads = 256;
-constexpr int kRhsMaxCols = 8;  // columns per thread: tj * nx <= 2048
+
 
 // CPT: columns per thread (tj * nx <= CPT * kRhsThreads)
 template <int CPT>
@@ -164,7 +166,8 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
   }
   __syncthreads();
 
-  float vmax = 0.0f;
+  float vmax = 0.0f, smax = 0.0f, wmax = 0.0f;
+  df fsum = {0.0f, 0.0f}, wsum = {0.0f, 0.0f};  // sum of f, wall flux v*(ny) - v*(0)
   for (int st = 0; st < steps; ++st) {
     const int k = k0 + st;
     const bool more = st + 1 < steps;
@@ -223,6 +226,8 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
             if (j == 0 || j == ny) {
               q = df_norm(df_mulz(K.cy, vs));
               if (own && out.vpre) out.vpre[cvv] = vs;
+              wsum = (j == ny) ? df_addz(wsum, vs) : df_subz(wsum, vs);
+              wmax = fmaxf(wmax, fabsf(vs.hi));
             } else {
               const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
               const FaceOut fo = face_q(R[rl], R[rh], P[rl], P[rh], vs, K.cy, K.gy, K, rule);
@@ -256,7 +261,10 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       const df dyq = df_mulz(df_subz(QY[(jj + 1) * nx + i], QY[jj * nx + i]), K.ly);
       const df dzq = df_mulz(df_subz(QZup[u], QZ[u]), K.lz);
       const uint32_t c = cell(k, j0 + jj, i);
-      const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, d2df(ss_[u]))));
+      const df sv = d2df(ss_[u]);
+      const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, sv)));
+      fsum = df_addz(fsum, f);
+      smax = fmaxf(smax, fabsf(sv.hi));
       if (out.fdf) out.fdf[c] = f;
       if (out.f64) out.f64[c] = df2d(f);
       vmax = fmaxf(vmax, fabsf(f.hi));
@@ -282,7 +290,15 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
     }
   }
   block_max_to(&sc->fmax_bits, vmax);
+  block_max_to(&sc->smax_bits, smax);
+  block_max_to(&sc->wallv_bits, wmax);
+  // per-CTA sums of f and of the wall flux; their totals are formed in a fixed
+  // order by the next kernel (finish_rhs_sums), so no grid-wide fence here
+  block_pair_sums(fsum, wsum, sc->part + blockIdx.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->rhs_parts = (int)gridDim.x;
 }
+
+__global__ void k_finish_rhs(GridDev g, DevScalars* sc) { finish_rhs_sums(sc, g); }
 
 size_t rhs_smem(int nx, int tj) {
   const size_t nl = tj + 2;
@@ -319,12 +335,42 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
   return cudaGetLastError();
 }
 
+namespace {
+// Opt-in dynamic shared memory of one instance: the per-CTA maximum minus the
+// instance's static shared memory (the reduction scratch).
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t* dyn_max) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  const size_t cap = kSmemPerCta - a.sharedSizeBytes;
+  if (dyn_max && cap < *dyn_max) *dyn_max = cap;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}
+}  // namespace
+
+cudaError_t launch_finish_rhs(const GridDev& g, DevScalars* sc, cudaStream_t st) {
+  k_finish_rhs<<<1, 256, 0, st>>>(g, sc);
+  return cudaGetLastError();
+}
+
 cudaError_t set_rhs_smem_limit() {
-  cudaError_t e = cudaFuncSetAttribute(k_rhs_march<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rhs_march<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  size_t cap = kSmemPerCta;
+  cudaError_t e = raise_smem(k_rhs_march<1>, &cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<2>, &cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<4>, &cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<8>, &cap);
   return e;
+}
+
+size_t rhs_smem_limit() {
+  size_t cap = kSmemPerCta;
+  if (set_rhs_smem_limit() != cudaSuccess) return 0;
+  raise_smem(k_rhs_march<1>, &cap);
+  raise_smem(k_rhs_march<2>, &cap);
+  raise_smem(k_rhs_march<4>, &cap);
+  raise_smem(k_rhs_march<8>, &cap);
+  return cap;
 }
 
 }  // namespace ppe

@@ -102,6 +102,11 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
     lc[2] = sc->K.lz;
   }
   float vmax = 0.0f;
+  df fmean = {0.0f, 0.0f};  // SRC_RESID: mean of f, left out of the residual (the solve drops it)
+  if (SRC == SRC_RESID) fmean = sc->f_mean;
+  df fsum = {0.0f, 0.0f};  // SRC_F: sum of f over this thread's cells
+  // SRC_FDF: f comes from k_rhs_march; CTA 0 totals that kernel's partial sums
+  if (SRC == SRC_FDF && blockIdx.x == 0) finish_rhs_sums(sc, g);
   if (SRC == SRC_F) {
     for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
       const int ll = (int)fdiv(idx, g.fd_nx);
@@ -110,14 +115,15 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
       if (line < nlines) {
         const size_t c = (size_t)l0 * nx + idx;
         const double x = __ldg(in.f + c);
+        const df v = d2df(x);
         if (sizeof(T) == 8) {
           val = (T)x;
         } else {
-          const df v = d2df(x);
           if (fdf) fdf[c] = v;
           val = (T)df_to_f(v);
         }
-        vmax = fmaxf(vmax, fabsf(d2df(x).hi));
+        vmax = fmaxf(vmax, fabsf(v.hi));
+        fsum = df_addz(fsum, v);
       }
       line_re[idx + ll * 2] = val;  // line ll starts at 2*ll*lsc = ll*nx + 2*ll
     }
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
           const df lz = df_subz(df_subz(pzp[u], p0), df_subz(p0, pzm[u]));
           const df ly = df_subz(df_subz(pyp[u], p0), df_subz(p0, pym[u]));  // wall sides contribute 0
           const df lap = df_addz(df_addz(df_mulz(lx, lc[0]), df_mulz(ly, lc[1])), df_mulz(lz, lc[2]));
-          const float r = df_to_f(df_subz(fv[u], lap));
+          const float r = df_to_f(df_subz(df_subz(fv[u], fmean), lap));
           val = (T)r;
           vmax = fmaxf(vmax, fabsf(r));
         }
@@ -189,6 +195,11 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
   }
   if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
+  if (SRC == SRC_F) {
+    __threadfence();  // this CTA's ||f|| atomics before its ticket (the last CTA reads ||f||)
+    double tot, unused;
+    if (grid_sum2(sc->part, &sc->part_done, fsum, df{0.0f, 0.0f}, &tot, &unused)) set_f_mean(sc, g, tot);
+  }
   if (!DO_FFT) return;
   cp_async_wait_all();
   __syncthreads();
@@ -503,8 +514,20 @@ size_t xinv_smem(int nx, int lpb) {
 }
 
 template <typename T>
+size_t xpass_smem_limit() {
+  // every x-pass instance carries the same static reduction scratch (grid_sum2)
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_xfwd<T, SRC_F, true, 0>) != cudaSuccess) return 0;
+  return kSmemPerCta - a.sharedSizeBytes;
+}
+
+template <typename T>
 cudaError_t set_smem_limits() {
-  cudaError_t e = cudaFuncSetAttribute(k_ythomas<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k_ythomas<T>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ythomas<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemPerCta - a.sharedSizeBytes));
   if (e == cudaSuccess) e = set_rhs_smem_limit();
   return e;
 }
@@ -622,6 +645,7 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   template size_t zfft_smem<T>(int, int);                                                                        \
   template size_t xinv_smem<T>(int, int);                                                                        \
   template cudaError_t set_smem_limits<T>();                                                                     \
+  template size_t xpass_smem_limit<T>();                                                                         \
   template cudaError_t launch_xfwd<T>(int, bool, const GridDev&, const StencilIn&, DevScalars*, int, df*,       \
                                       const df*, cpx<T>*, const RadixPlan&, const cpx<T>*, int, cudaStream_t);  \
   template cudaError_t launch_zfft<T>(bool, const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, int,      \

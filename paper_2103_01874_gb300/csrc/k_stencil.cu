@@ -20,6 +20,16 @@ __global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep
   sc->iter = 1;
   sc->cont = 0;
   sc->tol = tol;
+  sc->part_done = 0u;
+  sc->f_sum = 0.0;
+  sc->f_mean = {0.0f, 0.0f};
+  sc->f_ran = 0;
+  if (!keep_rho0) {  // a call that assembles f: its compatibility sums start here
+    sc->smax_bits = 0ull;
+    sc->wallv_bits = 0ull;
+    sc->wall_flux = 0.0;
+    sc->rhs_ran = 0;
+  }
 }
 
 // rho > 0 (densities), so the IEEE bit patterns order like the values and the
@@ -189,10 +199,12 @@ __global__ void k_set_outputs(DevScalars* sc, double* p, double* u, double* v, d
 // Eq. (33) from u_pre as in k_correct_pre, with p as pairs, plus the residual
 // r = f - L p of that same p at every cell (max into rmax[iter + 1]), so that the
 // convergence test after a correction needs no separate pass.
-__global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* __restrict__ upre,
-                                                       const df* __restrict__ vpre, const df* __restrict__ wpre,
-                                                       const df* __restrict__ pdf, const df* __restrict__ fdf,
-                                                       DevScalars* sc) {
+// SUB: the mean of f is non-zero and is left out of the residual (the solve drops it)
+template <bool SUB>
+__device__ __forceinline__ void correct_check_body(const GridDev& g, const df* __restrict__ upre,
+                                                   const df* __restrict__ vpre, const df* __restrict__ wpre,
+                                                   const df* __restrict__ pdf, const df* __restrict__ fdf,
+                                                   DevScalars* sc, df fmean) {
   const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
   const uint32_t total = (uint32_t)g.nz * (ny + 1) * nx;
   const StencilConst K = sc->K;
@@ -254,10 +266,22 @@ __global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* _
       const df ly = df_subz(df_subz(pyp[u], q), df_subz(q, pym[u]));
       const df lz = df_subz(df_subz(pzp[u], q), df_subz(q, pzm[u]));
       const df lap = df_addz(df_addz(df_mulz(lx, K.lx), df_mulz(ly, K.ly)), df_mulz(lz, K.lz));
-      vmax = fmaxf(vmax, fabsf(df_to_f(df_subz(fv[u], lap))));
+      const df fr = SUB ? df_subz(fv[u], fmean) : fv[u];
+      vmax = fmaxf(vmax, fabsf(df_to_f(df_subz(fr, lap))));
     }
   }
   block_max_to(&sc->rmax_bits[slot], vmax);
+}
+
+__global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* __restrict__ upre,
+                                                       const df* __restrict__ vpre, const df* __restrict__ wpre,
+                                                       const df* __restrict__ pdf, const df* __restrict__ fdf,
+                                                       DevScalars* sc) {
+  const df fmean = sc->f_mean;
+  if (fmean.hi == 0.0f)
+    correct_check_body<false>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
+  else
+    correct_check_body<true>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
 }
 
 __global__ void k_make_const(GridDev g, DevScalars* sc, double dt) {

@@ -43,6 +43,7 @@ struct ppe_plan_s {
   df* upre;           // explicitly split velocity u_pre on x faces (ppe_project)
   df* vpre;           //   ... on y faces
   df* wpre;           //   ... on z faces
+  double2* rhs_part;  // per-CTA partial sums of the right-hand-side kernel (ny * nz entries: any tiling)
   DevScalars* sc;
   // refinement loops as CUDA graphs with a WHILE conditional node (FP32_REFINE):
   // ppe_solve's and ppe_project's (the latter ends with the fused correction)
@@ -544,6 +545,7 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   b += (fp32 ? 16 : 8) * n;                                             // f (and p) as pairs
   b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
+  b += 16 * (size_t)g->ny * g->nz;                                       // right-hand-side partial sums
   return b;
 }
 
@@ -557,11 +559,13 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   o.face_rule = PPE_FACE_ARITHMETIC;
   o.refine_tol = 1e-10;
   o.max_sweeps = 6;
+  o.compat_tol = 1e-12;
   if (opt) o = *opt;
   if (o.precision != PPE_FP64 && o.precision != PPE_FP32_REFINE) return PPE_ERR_INVALID_ARG;
   if (o.face_rule != PPE_FACE_ARITHMETIC && o.face_rule != PPE_FACE_HARMONIC) return PPE_ERR_INVALID_ARG;
   if (o.max_sweeps < 0 || o.max_sweeps > kMaxSweeps) return PPE_ERR_INVALID_ARG;
   if (o.precision == PPE_FP32_REFINE && !(o.refine_tol >= 0)) return PPE_ERR_INVALID_ARG;
+  if (!(o.compat_tol >= 0)) return PPE_ERR_INVALID_ARG;
 
   ppe_plan_t P = new (std::nothrow) ppe_plan_s;
   if (!P) return PPE_ERR_OUT_OF_MEMORY;
@@ -611,8 +615,10 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, sizeof(double2) * g->ny * g->nz));
   P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 : 1) * sizeof(df) * ncell +
-                 sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz);
+                 sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz) +
+                 sizeof(double2) * g->ny * g->nz;
   choose_rhs_tiles(P);
   if (s == PPE_OK) {
     if (P->fp32) {
@@ -629,6 +635,9 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   }
   if (s == PPE_OK && P->fp32) s = build_refine_graphs(P);
   if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, 1.0, o.refine_tol, 0, P->stream));
+  if (s == PPE_OK)
+    s = cuda_status(cudaMemcpyAsync((char*)P->sc + offsetof(DevScalars, part), &P->rhs_part, sizeof(P->rhs_part),
+                                    cudaMemcpyHostToDevice, P->stream));
   // grid-only constants (1/dx^2 ...) for a ppe_solve that no ppe_rhs preceded
   if (s == PPE_OK) s = cuda_status(launch_make_const(P->gd, P->sc, 1.0, P->stream));
   if (s == PPE_OK) s = cuda_status(cudaStreamSynchronize(P->stream));
@@ -658,6 +667,7 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->line_off);
   cudaFree(P->line_len);
   cudaFree(P->fdf);
+  cudaFree(P->rhs_part);
   cudaFree(P->pdf);
   cudaFree(P->upre);
   cudaFree(P->vpre);
@@ -688,7 +698,8 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   auto pow2 = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
   const size_t lim = 227 * 1024;
   const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
-  if (!pow2(t->rhs_lines, 1, 8) || rhs_smem(nx, t->rhs_lines) > lim || t->rhs_lines > rhs_max_lines(nx))
+  if (!pow2(t->rhs_lines, 1, 8) || rhs_smem(nx, t->rhs_lines) > rhs_smem_limit() ||
+      t->rhs_lines > rhs_max_lines(nx))
     return PPE_ERR_INVALID_ARG;
   if (t->rhs_planes < 1 || t->rhs_planes > nz) return PPE_ERR_INVALID_ARG;
   if (!pow2(t->x_lines, 1, 64)) return PPE_ERR_INVALID_ARG;
@@ -699,7 +710,8 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
                                    ? xfwd_smem<double>(nx, t->x_lines) : xinv_smem<double>(nx, t->x_lines));
   const size_t zs = P->fp32 ? zfft_smem<float>(nz, t->z_cols) : zfft_smem<double>(nz, t->z_cols);
   const size_t ys = P->fp32 ? zfft_smem<float>(ny, t->y_cols) : 0;
-  if (xs > lim || zs > lim || ys > lim) return PPE_ERR_INVALID_ARG;
+  const size_t xlim = P->fp32 ? xpass_smem_limit<float>() : xpass_smem_limit<double>();
+  if (xs > xlim || zs > lim || ys > lim) return PPE_ERR_INVALID_ARG;
   PPE_TRY(cudaStreamSynchronize(P->stream));
   P->tj = t->rhs_lines;
   P->kc = t->rhs_planes;
@@ -751,6 +763,7 @@ ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double*
   if (!(rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(rho, n, P->sc, P->stream));
   PPE_TRY(launch_make_const(P->gd, P->sc, dt, P->stream));
   PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, P->tj, P->kc, P->stream));
+  PPE_TRY(launch_finish_rhs(P->gd, P->sc, P->stream));
   return PPE_OK;
 }
 
@@ -950,8 +963,8 @@ ppe_status ppe_project_host(ppe_plan_t P, const ppe_fields* H) {
   PPE_TRY(cudaMemcpyAsync(H->v_out, D.v_out, nv * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
   PPE_TRY(cudaMemcpyAsync(H->w_out, D.w_out, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
   if (H->f) PPE_TRY(cudaMemcpyAsync(H->f, D.f, n * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-  PPE_TRY(cudaStreamSynchronize(P->stream));
-  return PPE_OK;
+  ppe_info info;
+  return ppe_get_info(P, &info);  // synchronises; device-side status (convergence, compatibility)
 }
 
 ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
@@ -962,6 +975,25 @@ ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
   const double fmax = h.fmax_bits ? __builtin_bit_cast(double, h.fmax_bits) : 0.0;
   info->f_max = fmax;
   info->rho0 = __builtin_bit_cast(double, h.rho0_bits);
+  bool incompatible = false;
+  const double n = (double)P->g.nx * P->g.ny * P->g.nz;
+  if (h.rhs_ran) {
+    // Over the cells, sum D u* = sum over (i, k) of (v*(ny) - v*(0)) / dy (x, z
+    // periodic) and sum D(beta G p_hat) = 0 (G = 0 on the walls), so by Eq. (34)
+    // mean(S) = wall_flux_mean - (dt/rho_0) mean(f).
+    const double idy = P->g.ny / P->g.ly;
+    const double c = df2d(h.K.c);  // rho_0 / dt
+    info->f_mean_removed = h.f_sum / n;
+    info->wall_flux_mean = h.wall_flux * idy / n;
+    info->s_mean = info->wall_flux_mean - info->f_mean_removed / c;
+    info->s_absmax = h.smax_bits ? __builtin_bit_cast(double, h.smax_bits) : 0.0;
+    info->wall_vmax = h.wallv_bits ? __builtin_bit_cast(double, h.wallv_bits) : 0.0;
+  } else {
+    info->s_mean = info->s_absmax = info->wall_flux_mean = info->wall_vmax = NAN;
+    info->f_mean_removed = h.f_ran ? h.f_sum / n : NAN;
+  }
+  // the Neumann problem needs mean(f) = 0; what the solve drops, relative to ||f||
+  if (h.f_ran && P->opt.compat_tol > 0) incompatible = fabs(h.f_sum / n) > P->opt.compat_tol * fmax;
   if (P->fp32) {
     info->sweeps = h.sweeps;
     if (h.last_slot >= 0 && fmax > 0)
@@ -973,7 +1005,7 @@ ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
     info->sweeps = 0;
     info->rel_residual = -1.0;
   }
-  return PPE_OK;
+  return incompatible ? PPE_ERR_INCOMPATIBLE_RHS : PPE_OK;
 }
 
 }  // extern "C"

@@ -43,6 +43,18 @@ struct DevScalars {
   double* out_u;
   double* out_v;
   double* out_w;
+  // compatibility of the right-hand side and the mean of f, which the solve
+  // drops and the refinement residual leaves out
+  unsigned long long smax_bits;                 // max |S| (k_rhs_march)
+  unsigned long long wallv_bits;                // max |v*| on the wall faces y = 0, Ly (k_rhs_march)
+  double wall_flux;                             // sum over (i, k) of v*(ny) - v*(0)
+  double f_sum;                                 // sum of f over the cells
+  df f_mean;                                    // f_sum / (nx ny nz) as a pair; 0 when it is rounding noise
+  int rhs_ran;                                  // wall_flux, smax, wallv belong to the last assembly
+  int f_ran;                                    // f_sum, f_mean belong to the current call
+  int rhs_parts;                                // CTAs of the last k_rhs_march (its partials in part[])
+  unsigned int part_done;                       // CTAs finished (last-CTA reduction of grid_sum2)
+  double2* part;                                // per-CTA partial sums (ny * nz entries), plan workspace
 };
 
 struct GridDev {
@@ -73,9 +85,14 @@ enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
 // ---- launchers (k_rhs.cu) ----
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
                        df* vpre, df* wpre, int tj, int kc, cudaStream_t st);
+// Totals of the right-hand-side kernel's partial sums (f, wall flux) into sc
+// (one CTA); the forward x transform of f does the same in its CTA 0.
+cudaError_t launch_finish_rhs(const GridDev& g, DevScalars* sc, cudaStream_t st);
 size_t rhs_smem(int nx, int tj);
 int rhs_max_lines(int nx);  // tj * nx may not exceed the columns the threads of a CTA hold
 cudaError_t set_rhs_smem_limit();
+size_t rhs_smem_limit();  // largest dynamic shared memory every k_rhs_march instance accepts
+constexpr size_t kSmemPerCta = 227 * 1024;  // opt-in shared memory per CTA (static + dynamic)
 
 // ---- launchers (k_spectral.cu) ----
 template <typename T>
@@ -103,6 +120,8 @@ template <typename T>
 size_t xinv_smem(int nx, int lpb);
 template <typename T>
 cudaError_t set_smem_limits();
+template <typename T>
+size_t xpass_smem_limit();  // largest dynamic shared memory of the x passes (static scratch excluded)
 
 // ---- launchers (k_stencil.cu) ----
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st);

@@ -92,10 +92,116 @@ __device__ __forceinline__ Nbr neighbours(const GridDev& g, int i, int j, int k)
 }
 
 __device__ __forceinline__ void block_max_to(unsigned long long* slot, float v) {
-  // v >= 0; reduce over the warp in FP32, one FP64 atomic per warp (all lanes must call).
-  // The maxima only steer the refinement stop test, so the float hi part suffices.
+  // v >= 0; reduce over the warp in FP32, one FP64 atomic per warp with a
+  // non-zero maximum (all lanes must call).  The maxima only steer the
+  // refinement stop test and the reports, so the float hi part suffices.
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(slot, (unsigned long long)__double_as_longlong((double)v));
+  if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(slot, (unsigned long long)__double_as_longlong((double)v));
+}
+
+// Reduction of two per-thread pair values over the CTA (a fixed shuffle tree,
+// then the warps in index order); thread 0 stores the pair of totals in *out.
+// Every thread of the CTA must call it (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ void block_pair_sums(df a, df b, double2* out) {
+  __shared__ df red_s[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = df_norm(a);
+  b = df_norm(b);
+  for (int o = 16; o > 0; o >>= 1) {
+    a = df_add(a, {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)});
+    b = df_add(b, {__shfl_down_sync(0xffffffffu, b.hi, o), __shfl_down_sync(0xffffffffu, b.lo, o)});
+  }
+  if (lane == 0) {
+    red_s[0][wid] = a;
+    red_s[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = red_s[0][0];
+    b = red_s[1][0];
+    for (int w = 1; w < nw; ++w) {
+      a = df_add(a, red_s[0][w]);
+      b = df_add(b, red_s[1][w]);
+    }
+    *out = make_double2(df2d(a), df2d(b));
+  }
+}
+
+// Sum of part[0..n) in an order that depends only on n and blockDim.x (thread
+// t takes t, t + blockDim.x, ... in turn; then a fixed shuffle and warp tree).
+// Every thread of the CTA must call it; thread 0 gets the totals.
+__device__ __forceinline__ void sum_parts_fixed(const double2* part, int n, double* tx, double* ty) {
+  __shared__ double red_p[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 v = __ldcg(part + i);
+    x += v.x;
+    y += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  if (lane == 0) {
+    red_p[0][wid] = x;
+    red_p[1][wid] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    x = red_p[0][0];
+    y = red_p[1][0];
+    for (int w = 1; w < nw; ++w) {
+      x += red_p[0][w];
+      y += red_p[1][w];
+    }
+    *tx = x;
+    *ty = y;
+  }
+}
+
+// Grid-wide sums of two per-thread pair values within one kernel: per-CTA
+// partials in part[blockIdx.x], then the CTA that takes the last ticket on
+// *done adds them with sum_parts_fixed and resets *done.  Every thread must
+// call it.  Returns true in thread 0 of the last CTA, with the totals.
+__device__ __forceinline__ bool grid_sum2(double2* part, unsigned int* done, df a, df b, double* ta, double* tb) {
+  __shared__ bool last;
+  block_pair_sums(a, b, part + blockIdx.x);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  sum_parts_fixed(part, (int)gridDim.x, ta, tb);
+  if (threadIdx.x != 0) return false;
+  *done = 0u;
+  return true;
+}
+
+// f_mean from the sum of f: a mean below 2^-40 ||f||_inf is rounding noise of a
+// compatible right-hand side (its last bits depend on how the cells were
+// grouped into CTAs) and is not subtracted, which keeps the refinement's
+// result independent of the tile shapes.
+__device__ __forceinline__ void set_f_mean(DevScalars* sc, const GridDev& g, double f_sum) {
+  const double mean = f_sum / ((double)g.nx * (double)g.ny * (double)g.nz);
+  const double fmax = __longlong_as_double((long long)sc->fmax_bits);
+  sc->f_sum = f_sum;
+  sc->f_mean = (fabs(mean) > 0x1p-40 * fmax) ? d2df(mean) : df{0.0f, 0.0f};
+  sc->f_ran = 1;
+}
+
+// Totals of k_rhs_march's per-CTA partials (sum of f, wall flux); one CTA, all
+// threads.  Runs in a kernel after k_rhs_march (the kernel boundary orders it).
+__device__ __forceinline__ void finish_rhs_sums(DevScalars* sc, const GridDev& g) {
+  double fs, ws;
+  sum_parts_fixed(sc->part, sc->rhs_parts, &fs, &ws);
+  if (threadIdx.x == 0) {
+    sc->wall_flux = ws;
+    sc->rhs_ran = 1;
+    set_f_mean(sc, g, fs);
+  }
 }
 
 }  // namespace ppe

@@ -38,11 +38,14 @@ class Grid(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("precision", c_int), ("face_rule", c_int), ("refine_tol", c_double), ("max_sweeps", c_int)]
+    _fields_ = [("precision", c_int), ("face_rule", c_int), ("refine_tol", c_double), ("max_sweeps", c_int),
+                ("compat_tol", c_double)]
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("sweeps", c_int), ("rel_residual", c_double), ("f_max", c_double), ("rho0", c_double)]
+    _fields_ = [("sweeps", c_int), ("rel_residual", c_double), ("f_max", c_double), ("rho0", c_double),
+                ("s_mean", c_double), ("s_absmax", c_double), ("wall_flux_mean", c_double), ("wall_vmax", c_double),
+                ("f_mean_removed", c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -231,12 +234,12 @@ class Plan:
     """A libppe plan for one grid (ppe_plan / ppe_destroy)."""
 
     def __init__(self, nx, ny, nz, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi, precision=FP64,
-                 face_rule=FACE_ARITHMETIC, refine_tol=1e-10, max_sweeps=6, stream=None):
+                 face_rule=FACE_ARITHMETIC, refine_tol=1e-10, max_sweeps=6, stream=None, compat_tol=1e-12):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.lengths = (lx, ly, lz)
         self.precision = precision
         self.grid = Grid(nx, ny, nz, lx, ly, lz)
-        self.opts = Options(precision, face_rule, refine_tol, max_sweeps)
+        self.opts = Options(precision, face_rule, refine_tol, max_sweeps, compat_tol)
         h = c_void_p()
         _check(lib().ppe_plan(ctypes.byref(h), ctypes.byref(self.grid), ctypes.byref(self.opts),
                               c_void_p(_stream_handle(stream))), "ppe_plan")
@@ -290,10 +293,10 @@ class Plan:
         fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
         _check(lib().ppe_project_host(self._h, ctypes.byref(fc)), "ppe_project_host")
 
-    def info(self, allow_not_converged=False) -> Info:
+    def info(self, allow_not_converged=False, allow_incompatible=False) -> Info:
         inf = Info()
         code = lib().ppe_get_info(self._h, ctypes.byref(inf))
-        if code == 5 and allow_not_converged:
+        if (code == 5 and allow_not_converged) or (code == 3 and allow_incompatible):
             return inf
         _check(code, "ppe_get_info")
         return inf

@@ -226,7 +226,7 @@ class CudaExecutor:
         import ctypes
         nx, ny, nz = shape
         g = self.ppe.Grid(nx, ny, nz, 1.0, 1.0, 1.0)
-        o = self.ppe.Options(precision, 0, 1e-10, 8)
+        o = self.ppe.Options(precision, 0, 1e-10, 8, 1e-12)
         return int(self.ppe.lib().ppe_workspace_bytes(ctypes.byref(g), ctypes.byref(o)))
 
     def plan_bytes(self, plan):

@@ -53,8 +53,8 @@ def test_host_only_calls(lib):
     for code in range(8):
         assert lib.ppe_strerror(code)
     g = ppe.Grid(256, 256, 256, 1.0, 1.0, 1.0)
-    o64 = ppe.Options(ppe.FP64, 0, 1e-10, 4)
-    o32 = ppe.Options(ppe.FP32_REFINE, 0, 1e-10, 4)
+    o64 = ppe.Options(ppe.FP64, 0, 1e-10, 4, 1e-12)
+    o32 = ppe.Options(ppe.FP32_REFINE, 0, 1e-10, 4, 1e-12)
     import ctypes
     b64 = lib.ppe_workspace_bytes(ctypes.byref(g), ctypes.byref(o64))
     b32 = lib.ppe_workspace_bytes(ctypes.byref(g), ctypes.byref(o32))

@@ -288,3 +288,47 @@ def test_planted_split_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O, "ppe_rhs", bad)
     out = O.ppe_project(fl.u, fl.v, fl.w, fl.S, fl.rho, q, q, fl.dt, LENGTHS)
     assert O.rel_linf(out["p"], q) > 1e-3
+
+
+def _incompatible(fl, s_shift=0.05, v_top=0.3, v_bot=-0.1):
+    """Fields with wall flux and a shifted S: sum of (D u* - S) no longer vanishes."""
+    v = fl.v.copy()
+    v[:, -1, :] = v_top
+    v[:, 0, :] = v_bot
+    return v, fl.S + s_shift
+
+
+def test_compatibility_against_assembled_f():
+    """The compatibility quantities predict mean(f) of the assembled Eq. (34)
+    right-hand side (divergence theorem on the periodic/wall box), including
+    wall flux and a non-zero mean of S; the solve then drops exactly that mean."""
+    fl = _fields(seed=11)
+    v, S = _incompatible(fl)
+    rho0 = O.rho0_of(fl.rho)
+    f = O.ppe_rhs(fl.u, v, fl.w, S, fl.rho, fl.p_n, fl.p_nm1, rho0, fl.dt, LENGTHS)
+    c = O.compatibility(v, S, LENGTHS)
+    predicted = (rho0 / fl.dt) * (c["wall_flux_mean"] - c["s_mean"])
+    assert abs(f.mean() - predicted) <= 1e-12 * np.abs(f).max()
+    assert abs(predicted) > 1e-3 * np.abs(f).max()   # the case is really incompatible
+    assert c["wall_vmax"] == 0.3 and c["s_absmax"] == np.abs(S).max()
+    # generated fields are compatible: no wall flux, S mean removed
+    c0 = O.compatibility(fl.v, fl.S, LENGTHS)
+    assert c0["wall_vmax"] == 0.0 and abs(c0["s_mean"]) <= 1e-15 * c0["s_absmax"]
+
+
+def test_planted_wall_flux_sign_is_caught(monkeypatch):
+    """A flipped wall-flux sign must disagree with the assembled f."""
+    good = O.compatibility
+
+    def bad(v, S, lengths):
+        c = good(v, S, lengths)
+        c["wall_flux_mean"] = -c["wall_flux_mean"]
+        return c
+    monkeypatch.setattr(O, "compatibility", bad)
+    fl = _fields(seed=11)
+    v, S = _incompatible(fl)
+    rho0 = O.rho0_of(fl.rho)
+    f = O.ppe_rhs(fl.u, v, fl.w, S, fl.rho, fl.p_n, fl.p_nm1, rho0, fl.dt, LENGTHS)
+    c = O.compatibility(v, S, LENGTHS)
+    predicted = (rho0 / fl.dt) * (c["wall_flux_mean"] - c["s_mean"])
+    assert abs(f.mean() - predicted) > 1e-3 * np.abs(f).max()
