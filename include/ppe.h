@@ -106,7 +106,8 @@ typedef struct {
     double f_max;         /* ||f||_inf of the last right-hand side (-1 if not computed) */
     double rho0;          /* rho_0 used by the last ppe_rhs / ppe_project */
     /* Compatibility of the last assembled right-hand side (NaN if no ppe_rhs /
-     * ppe_project ran since the plan was made; f_mean_removed also after ppe_solve): */
+     * ppe_project ran since the plan was made).  f_mean_removed and s_mean need
+     * the sum of f, which the solve forms: after ppe_rhs alone they are NaN. */
     double s_mean;          /* mean of S over the cells, from the divergence theorem:
                              * sum over cells of D u* keeps only the wall faces and
                              * sum D(beta G p_hat) = 0, so by Eq. (34)

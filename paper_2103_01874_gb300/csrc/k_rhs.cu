@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
   __syncthreads();
 
   float vmax = 0.0f, smax = 0.0f, wmax = 0.0f;
-  df fsum = {0.0f, 0.0f}, wsum = {0.0f, 0.0f};  // sum of f, wall flux v*(ny) - v*(0)
+  df wsum = {0.0f, 0.0f};  // wall flux v*(ny) - v*(0) of this CTA's wall faces
   for (int st = 0; st < steps; ++st) {
     const int k = k0 + st;
     const bool more = st + 1 < steps;
@@ -263,7 +263,6 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       const uint32_t c = cell(k, j0 + jj, i);
       const df sv = d2df(ss_[u]);
       const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, sv)));
-      fsum = df_addz(fsum, f);
       smax = fmaxf(smax, fabsf(sv.hi));
       if (out.fdf) out.fdf[c] = f;
       if (out.f64) out.f64[c] = df2d(f);
@@ -292,13 +291,16 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
   block_max_to(&sc->fmax_bits, vmax);
   block_max_to(&sc->smax_bits, smax);
   block_max_to(&sc->wallv_bits, wmax);
-  // per-CTA sums of f and of the wall flux; their totals are formed in a fixed
-  // order by the next kernel (finish_rhs_sums), so no grid-wide fence here
-  block_pair_sums(fsum, wsum, sc->part + blockIdx.x);
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->rhs_parts = (int)gridDim.x;
+  // wall tiles: the CTA's wall flux, totalled in a fixed order by a later
+  // kernel (finish_sums), so no grid-wide fence here
+  if (j0 == 0 || j0 + tj >= ny) block_pair_sums(wsum, df{0.0f, 0.0f}, sc->part + blockIdx.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rhs_tiles = ntile;
+    sc->rhs_chunks = (nz + kc - 1) / kc;
+  }
 }
 
-__global__ void k_finish_rhs(GridDev g, DevScalars* sc) { finish_rhs_sums(sc, g); }
+__global__ void k_finish_sums(GridDev g, DevScalars* sc) { finish_sums(sc, g); }
 
 size_t rhs_smem(int nx, int tj) {
   const size_t nl = tj + 2;
@@ -349,8 +351,8 @@ cudaError_t raise_smem(K kernel, size_t* dyn_max) {
 }
 }  // namespace
 
-cudaError_t launch_finish_rhs(const GridDev& g, DevScalars* sc, cudaStream_t st) {
-  k_finish_rhs<<<1, 256, 0, st>>>(g, sc);
+cudaError_t launch_finish_sums(const GridDev& g, DevScalars* sc, cudaStream_t st) {
+  k_finish_sums<<<1, 256, 0, st>>>(g, sc);
   return cudaGetLastError();
 }
 

@@ -104,9 +104,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
   float vmax = 0.0f;
   df fmean = {0.0f, 0.0f};  // SRC_RESID: mean of f, left out of the residual (the solve drops it)
   if (SRC == SRC_RESID) fmean = sc->f_mean;
-  df fsum = {0.0f, 0.0f};  // SRC_F: sum of f over this thread's cells
-  // SRC_FDF: f comes from k_rhs_march; CTA 0 totals that kernel's partial sums
-  if (SRC == SRC_FDF && blockIdx.x == 0) finish_rhs_sums(sc, g);
+  df fsum = {0.0f, 0.0f};  // SRC_F / SRC_FDF: sum of f over this thread's cells
   if (SRC == SRC_F) {
     for (int idx = threadIdx.x; idx < lpb * nx; idx += blockDim.x) {
       const int ll = (int)fdiv(idx, g.fd_nx);
@@ -145,6 +143,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         if (idx >= lpb * nx) continue;
         const int ll = (int)fdiv(idx, g.fd_nx);
         line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d(v[u]) : (T)df_to_f(v[u]);
+        fsum = df_addz(fsum, v[u]);
       }
     }
   } else {
@@ -195,10 +194,10 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
   }
   if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
-  if (SRC == SRC_F) {
-    __threadfence();  // this CTA's ||f|| atomics before its ticket (the last CTA reads ||f||)
-    double tot, unused;
-    if (grid_sum2(sc->part, &sc->part_done, fsum, df{0.0f, 0.0f}, &tot, &unused)) set_f_mean(sc, g, tot);
+  if (SRC == SRC_F || SRC == SRC_FDF) {
+    // per-CTA sum of f, totalled in a fixed order by the next kernel (finish_sums)
+    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->x_parts = (int)gridDim.x;
   }
   if (!DO_FFT) return;
   cp_async_wait_all();
@@ -226,8 +225,9 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
 // ---------------------------------------------------------------------------
 template <typename T, bool INV, int N>
 __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
-                                              int tkx, const DevScalars* sc) {
+                                              int tkx, const DevScalars* sc, DevScalars* fin) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (fin && blockIdx.x == 0) finish_sums(fin, g);  // uniform over the CTA
   if (sc && sc->done) return;
   const int nz = g.nz, nxh = g.nx / 2 + 1;
   const int ntile = (nxh + tkx - 1) / tkx;
@@ -515,9 +515,17 @@ size_t xinv_smem(int nx, int lpb) {
 
 template <typename T>
 size_t xpass_smem_limit() {
-  // every x-pass instance carries the same static reduction scratch (grid_sum2)
+  // every x-pass instance carries the same static reduction scratch (block_pair_sums)
   cudaFuncAttributes a;
   if (cudaFuncGetAttributes(&a, k_xfwd<T, SRC_F, true, 0>) != cudaSuccess) return 0;
+  return kSmemPerCta - a.sharedSizeBytes;
+}
+
+template <typename T>
+size_t zpass_smem_limit() {
+  // the z pass carries the static scratch of finish_sums
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_zfft<T, false, 0>) != cudaSuccess) return 0;
   return kSmemPerCta - a.sharedSizeBytes;
 }
 
@@ -561,7 +569,7 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
 
 template <typename T>
 cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw,
-                        int tkx, const DevScalars* sc, cudaStream_t st) {
+                        int tkx, const DevScalars* sc, DevScalars* fin, cudaStream_t st) {
   const int nxh = g.nx / 2 + 1;
   const int grid = g.ny * ((nxh + tkx - 1) / tkx);
   const size_t sm = zfft_smem<T>(g.nz, tkx);
@@ -570,10 +578,10 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
     cudaError_t e;
     if (inverse) {
       if ((e = allow_smem(k_zfft<T, true, N>, sm)) != cudaSuccess) return e;
-      k_zfft<T, true, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
+      k_zfft<T, true, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc, fin);
     } else {
       if ((e = allow_smem(k_zfft<T, false, N>, sm)) != cudaSuccess) return e;
-      k_zfft<T, false, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc);
+      k_zfft<T, false, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc, fin);
     }
     return cudaGetLastError();
   });
@@ -649,7 +657,8 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   template cudaError_t launch_xfwd<T>(int, bool, const GridDev&, const StencilIn&, DevScalars*, int, df*,       \
                                       const df*, cpx<T>*, const RadixPlan&, const cpx<T>*, int, cudaStream_t);  \
   template cudaError_t launch_zfft<T>(bool, const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, int,      \
-                                      const DevScalars*, cudaStream_t);                                          \
+                                      const DevScalars*, DevScalars*, cudaStream_t);                             \
+  template size_t zpass_smem_limit<T>();                                                                         \
   template cudaError_t launch_ythomas<T>(const GridDev&, cpx<T>*, const T*, const int*, const int*, T,          \
                                          const DevScalars*, cudaStream_t);                                       \
   template cudaError_t launch_ydct<T>(const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, const cpx<T>*,     \

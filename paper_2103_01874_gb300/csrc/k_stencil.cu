@@ -20,15 +20,17 @@ __global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep
   sc->iter = 1;
   sc->cont = 0;
   sc->tol = tol;
-  sc->part_done = 0u;
   sc->f_sum = 0.0;
   sc->f_mean = {0.0f, 0.0f};
   sc->f_ran = 0;
+  sc->x_parts = 0;
   if (!keep_rho0) {  // a call that assembles f: its compatibility sums start here
     sc->smax_bits = 0ull;
     sc->wallv_bits = 0ull;
     sc->wall_flux = 0.0;
     sc->rhs_ran = 0;
+    sc->rhs_tiles = 0;
+    sc->rhs_chunks = 0;
   }
 }
 

@@ -43,7 +43,7 @@ struct ppe_plan_s {
   df* upre;           // explicitly split velocity u_pre on x faces (ppe_project)
   df* vpre;           //   ... on y faces
   df* wpre;           //   ... on z faces
-  double2* rhs_part;  // per-CTA partial sums of the right-hand-side kernel (ny * nz entries: any tiling)
+  double2* rhs_part;  // per-CTA partial sums (2 ny nz entries: right-hand side, x transform; any tiling)
   DevScalars* sc;
   // refinement loops as CUDA graphs with a WHILE conditional node (FP32_REFINE):
   // ppe_solve's and ppe_project's (the latter ends with the fused correction)
@@ -319,7 +319,10 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   const DevScalars* sc = guarded ? P->sc : nullptr;
   cpx<T>* spec = (cpx<T>*)P->spec;
   const double scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
-  PPE_LAUNCH(P, K_ZFFT_FWD, launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
+  // the first pass after an x transform of f also totals the partial sums (finish_sums)
+  DevScalars* fin = guarded ? nullptr : P->sc;
+  PPE_LAUNCH(P, K_ZFFT_FWD,
+             launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, fin, P->stream));
   if (P->fp32) {
     const T* lam = (const T*)P->lam;
     PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
@@ -328,7 +331,8 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
     PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y,
                                                sc, P->stream));
   }
-  PPE_LAUNCH(P, K_ZFFT_INV, launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, P->stream));
+  PPE_LAUNCH(P, K_ZFFT_INV,
+             launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, nullptr, P->stream));
   PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
              launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
                             P->stream));
@@ -545,7 +549,7 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   b += (fp32 ? 16 : 8) * n;                                             // f (and p) as pairs
   b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
-  b += 16 * (size_t)g->ny * g->nz;                                       // right-hand-side partial sums
+  b += 32 * (size_t)g->ny * g->nz;                                       // per-CTA partial sums
   return b;
 }
 
@@ -615,10 +619,10 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
-  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, sizeof(double2) * g->ny * g->nz));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, 2 * sizeof(double2) * g->ny * g->nz));
   P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 : 1) * sizeof(df) * ncell +
                  sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz) +
-                 sizeof(double2) * g->ny * g->nz;
+                 2 * sizeof(double2) * g->ny * g->nz;
   choose_rhs_tiles(P);
   if (s == PPE_OK) {
     if (P->fp32) {
@@ -711,7 +715,8 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   const size_t zs = P->fp32 ? zfft_smem<float>(nz, t->z_cols) : zfft_smem<double>(nz, t->z_cols);
   const size_t ys = P->fp32 ? zfft_smem<float>(ny, t->y_cols) : 0;
   const size_t xlim = P->fp32 ? xpass_smem_limit<float>() : xpass_smem_limit<double>();
-  if (xs > xlim || zs > lim || ys > lim) return PPE_ERR_INVALID_ARG;
+  const size_t zlim = P->fp32 ? zpass_smem_limit<float>() : zpass_smem_limit<double>();
+  if (xs > xlim || zs > zlim || ys > lim) return PPE_ERR_INVALID_ARG;
   PPE_TRY(cudaStreamSynchronize(P->stream));
   P->tj = t->rhs_lines;
   P->kc = t->rhs_planes;
@@ -763,7 +768,7 @@ ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double*
   if (!(rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(rho, n, P->sc, P->stream));
   PPE_TRY(launch_make_const(P->gd, P->sc, dt, P->stream));
   PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, f, nullptr, nullptr, nullptr, nullptr, P->tj, P->kc, P->stream));
-  PPE_TRY(launch_finish_rhs(P->gd, P->sc, P->stream));
+  PPE_TRY(launch_finish_sums(P->gd, P->sc, P->stream));
   return PPE_OK;
 }
 
@@ -977,20 +982,17 @@ ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
   info->rho0 = __builtin_bit_cast(double, h.rho0_bits);
   bool incompatible = false;
   const double n = (double)P->g.nx * P->g.ny * P->g.nz;
+  const double idy = P->g.ny / P->g.ly;
+  info->s_absmax = info->wall_flux_mean = info->wall_vmax = info->s_mean = NAN;
+  info->f_mean_removed = h.f_ran ? h.f_sum / n : NAN;
   if (h.rhs_ran) {
+    info->wall_flux_mean = h.wall_flux * idy / n;
+    info->s_absmax = h.smax_bits ? __builtin_bit_cast(double, h.smax_bits) : 0.0;
+    info->wall_vmax = h.wallv_bits ? __builtin_bit_cast(double, h.wallv_bits) : 0.0;
     // Over the cells, sum D u* = sum over (i, k) of (v*(ny) - v*(0)) / dy (x, z
     // periodic) and sum D(beta G p_hat) = 0 (G = 0 on the walls), so by Eq. (34)
     // mean(S) = wall_flux_mean - (dt/rho_0) mean(f).
-    const double idy = P->g.ny / P->g.ly;
-    const double c = df2d(h.K.c);  // rho_0 / dt
-    info->f_mean_removed = h.f_sum / n;
-    info->wall_flux_mean = h.wall_flux * idy / n;
-    info->s_mean = info->wall_flux_mean - info->f_mean_removed / c;
-    info->s_absmax = h.smax_bits ? __builtin_bit_cast(double, h.smax_bits) : 0.0;
-    info->wall_vmax = h.wallv_bits ? __builtin_bit_cast(double, h.wallv_bits) : 0.0;
-  } else {
-    info->s_mean = info->s_absmax = info->wall_flux_mean = info->wall_vmax = NAN;
-    info->f_mean_removed = h.f_ran ? h.f_sum / n : NAN;
+    if (h.f_ran) info->s_mean = info->wall_flux_mean - info->f_mean_removed / df2d(h.K.c);
   }
   // the Neumann problem needs mean(f) = 0; what the solve drops, relative to ||f||
   if (h.f_ran && P->opt.compat_tol > 0) incompatible = fabs(h.f_sum / n) > P->opt.compat_tol * fmax;

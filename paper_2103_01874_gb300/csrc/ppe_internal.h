@@ -52,9 +52,11 @@ struct DevScalars {
   df f_mean;                                    // f_sum / (nx ny nz) as a pair; 0 when it is rounding noise
   int rhs_ran;                                  // wall_flux, smax, wallv belong to the last assembly
   int f_ran;                                    // f_sum, f_mean belong to the current call
-  int rhs_parts;                                // CTAs of the last k_rhs_march (its partials in part[])
-  unsigned int part_done;                       // CTAs finished (last-CTA reduction of grid_sum2)
-  double2* part;                                // per-CTA partial sums (ny * nz entries), plan workspace
+  int rhs_tiles, rhs_chunks;                    // tiling of the last k_rhs_march (0: none this call)
+  int x_parts;                                  // CTAs of the last forward x transform of f (0: none)
+  double2* part;                                // per-CTA partial sums, plan workspace (2 ny nz entries):
+                                                //   [0, ny nz): k_rhs_march (wall flux, wall tiles only)
+                                                //   [ny nz, 2 ny nz): forward x transform (sum of f)
 };
 
 struct GridDev {
@@ -85,9 +87,9 @@ enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
 // ---- launchers (k_rhs.cu) ----
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
                        df* vpre, df* wpre, int tj, int kc, cudaStream_t st);
-// Totals of the right-hand-side kernel's partial sums (f, wall flux) into sc
-// (one CTA); the forward x transform of f does the same in its CTA 0.
-cudaError_t launch_finish_rhs(const GridDev& g, DevScalars* sc, cudaStream_t st);
+// Totals of the per-CTA partial sums into sc (one CTA, finish_sums); the first
+// forward z pass after an x transform of f does the same in its CTA 0.
+cudaError_t launch_finish_sums(const GridDev& g, DevScalars* sc, cudaStream_t st);
 size_t rhs_smem(int nx, int tj);
 int rhs_max_lines(int nx);  // tj * nx may not exceed the columns the threads of a CTA hold
 cudaError_t set_rhs_smem_limit();
@@ -99,9 +101,11 @@ template <typename T>
 cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn& in, DevScalars* sc,
                         int sweep_slot, df* fdf, const df* pdf, cpx<T>* spec, const RadixPlan& rp_half,
                         const cpx<T>* tw_x, int lpb, cudaStream_t st);
+// fin: non-NULL on the first forward pass after an x transform of f: its CTA 0
+// forms the totals of the partial sums (finish_sums) before its own work.
 template <typename T>
 cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const RadixPlan& rp,
-                        const cpx<T>* tw_z, int tkx, const DevScalars* sc, cudaStream_t st);
+                        const cpx<T>* tw_z, int tkx, const DevScalars* sc, DevScalars* fin, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* line_off,
                            const int* line_len, T a, const DevScalars* sc, cudaStream_t st);
@@ -122,6 +126,8 @@ template <typename T>
 cudaError_t set_smem_limits();
 template <typename T>
 size_t xpass_smem_limit();  // largest dynamic shared memory of the x passes (static scratch excluded)
+template <typename T>
+size_t zpass_smem_limit();  // the same for the z pass
 
 // ---- launchers (k_stencil.cu) ----
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st);

@@ -160,47 +160,37 @@ __device__ __forceinline__ void sum_parts_fixed(const double2* part, int n, doub
   }
 }
 
-// Grid-wide sums of two per-thread pair values within one kernel: per-CTA
-// partials in part[blockIdx.x], then the CTA that takes the last ticket on
-// *done adds them with sum_parts_fixed and resets *done.  Every thread must
-// call it.  Returns true in thread 0 of the last CTA, with the totals.
-__device__ __forceinline__ bool grid_sum2(double2* part, unsigned int* done, df a, df b, double* ta, double* tb) {
-  __shared__ bool last;
-  block_pair_sums(a, b, part + blockIdx.x);
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  sum_parts_fixed(part, (int)gridDim.x, ta, tb);
-  if (threadIdx.x != 0) return false;
-  *done = 0u;
-  return true;
-}
-
-// f_mean from the sum of f: a mean below 2^-40 ||f||_inf is rounding noise of a
-// compatible right-hand side (its last bits depend on how the cells were
-// grouped into CTAs) and is not subtracted, which keeps the refinement's
-// result independent of the tile shapes.
-__device__ __forceinline__ void set_f_mean(DevScalars* sc, const GridDev& g, double f_sum) {
-  const double mean = f_sum / ((double)g.nx * (double)g.ny * (double)g.nz);
-  const double fmax = __longlong_as_double((long long)sc->fmax_bits);
-  sc->f_sum = f_sum;
-  sc->f_mean = (fabs(mean) > 0x1p-40 * fmax) ? d2df(mean) : df{0.0f, 0.0f};
-  sc->f_ran = 1;
-}
-
-// Totals of k_rhs_march's per-CTA partials (sum of f, wall flux); one CTA, all
-// threads.  Runs in a kernel after k_rhs_march (the kernel boundary orders it).
-__device__ __forceinline__ void finish_rhs_sums(DevScalars* sc, const GridDev& g) {
-  double fs, ws;
-  sum_parts_fixed(sc->part, sc->rhs_parts, &fs, &ws);
-  if (threadIdx.x == 0) {
+// Totals of the per-CTA partial sums of the current call, formed by one CTA
+// (all threads) in a kernel that runs after their producers (the kernel
+// boundary orders the accesses): the sum of f from the forward x transform
+// (sum_parts_fixed over its CTAs) and the wall flux from the wall tiles of
+// k_rhs_march (chunk by chunk, lower wall then upper wall).
+__device__ __forceinline__ void finish_sums(DevScalars* sc, const GridDev& g) {
+  const size_t nynz = (size_t)g.ny * g.nz;
+  const int xp = sc->x_parts;
+  double fs = 0.0, unused;
+  if (xp > 0) sum_parts_fixed(sc->part + nynz, xp, &fs, &unused);
+  if (threadIdx.x != 0) return;
+  const int nt = sc->rhs_tiles, nc = sc->rhs_chunks;
+  if (nt > 0) {
+    double ws = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      ws += sc->part[(size_t)c * nt].x;
+      if (nt > 1) ws += sc->part[(size_t)c * nt + nt - 1].x;
+    }
     sc->wall_flux = ws;
     sc->rhs_ran = 1;
-    set_f_mean(sc, g, fs);
+  }
+  if (xp > 0) {
+    // A mean below 2^-40 ||f||_inf is rounding noise of a compatible right-hand
+    // side (its last bits depend on how the cells were grouped into CTAs); it is
+    // not subtracted, which keeps the refinement's result independent of the
+    // tile shapes.
+    const double mean = fs / ((double)g.nx * (double)g.ny * (double)g.nz);
+    const double fmax = __longlong_as_double((long long)sc->fmax_bits);
+    sc->f_sum = fs;
+    sc->f_mean = (fabs(mean) > 0x1p-40 * fmax) ? d2df(mean) : df{0.0f, 0.0f};
+    sc->f_ran = 1;
   }
 }
 

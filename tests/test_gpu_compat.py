@@ -151,3 +151,34 @@ def test_project_host_returns_the_device_status():
         assert e.value.code == 3
         plan.project_host(fl.u, fl.v, fl.w, fl.S, fl.rho, fl.p_n, fl.p_nm1, fl.dt, out["p"], out["u"], out["v"],
                           out["w"])
+
+
+def test_separate_rhs_then_solve_reports():
+    """ppe_rhs alone reports the wall flux and max |S| (the sum of f is formed by
+    the solve); the following ppe_solve adds the mean of f and the mean of S."""
+    import torch
+    from _gpu_util import dev_fields, to_dev
+    fl = fields.make_fields(32, 16, 24, seed=26, recipe="single", width=2.0)
+    L = (fl.lx, fl.ly, fl.lz)
+    v, S = _incompatible(fl)
+    d = dev_fields(fl)
+    d["v"], d["S"] = to_dev(v), to_dev(S)
+    f = torch.empty_like(d["rho"])
+    p = torch.empty_like(d["rho"])
+    c = O.compatibility(v, S, L)
+    ref_f = O.ppe_rhs(fl.u, v, fl.w, S, fl.rho, fl.p_n, fl.p_nm1, O.rho0_of(fl.rho), fl.dt, L)
+    dy = fl.ly / fl.ny
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, *L) as plan:
+        plan.rhs(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, f)
+        info = plan.info()
+        assert abs(info.wall_flux_mean - c["wall_flux_mean"]) <= 1e-14 * c["wall_vmax"] / dy
+        assert c["s_absmax"] * (1 - F32_TRUNC) <= info.s_absmax <= c["s_absmax"]
+        assert math.isnan(info.s_mean) and math.isnan(info.f_mean_removed)
+        plan.solve(f, p)
+        info = plan.info(allow_incompatible=True)
+        fmax = np.abs(ref_f).max()
+        assert abs(info.f_mean_removed - ref_f.mean()) <= 1e-12 * fmax
+        assert abs(info.s_mean - c["s_mean"]) <= 1e-12 * c["s_absmax"]
+        with pytest.raises(ppe.PPEError) as e:
+            plan.info()
+        assert e.value.code == 3
