@@ -170,6 +170,29 @@ def step_min_bytes(fp32: bool, sweeps: int) -> float:
 
 
 # ---------------------------------------------------------------------------
+# Replicas (one independent projection per rank, no data-path collective)
+# ---------------------------------------------------------------------------
+def replica_seed(rank: int) -> int:
+    """Each rank projects its own seeded fields (the replicas share nothing)."""
+    return 2 + rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The job's time is the slowest rank's (MAX all-reduce; identity for one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, ms_max: float) -> float:
+    """Projections per second of the whole job: every rank ran `steps` in at most ms_max."""
+    return world * steps / (ms_max * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -190,9 +213,9 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
 
     if NX == 256:
-        fl = fields.multimode_256(seed=2 + rank)
+        fl = fields.multimode_256(seed=replica_seed(rank))
     else:
-        fl = fields.make_fields(NX, NY, NZ, seed=2 + rank, recipe="multimode", width=6.0, rho_g=60.0)
+        fl = fields.make_fields(NX, NY, NZ, seed=replica_seed(rank), recipe="multimode", width=6.0, rho_g=60.0)
     d = {k: torch.from_numpy(v).to(dev) for k, v in fl.arrays().items()}
     c = fl.shape
     out = dict(p=torch.empty(c, dtype=torch.float64, device=dev), u=torch.empty_like(d["u"]),
@@ -227,11 +250,7 @@ def run_gpu(args):
         ms = e0.elapsed_time(e1)
         kt = plan.profile_read() if profile else {}
         plan.profile(False)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, kt
+        return max_over_ranks(ms, dist, dev), kt
 
     steps, warmup = args.steps, args.warmup
     forms = set(args.forms.split(","))
@@ -274,10 +293,7 @@ def run_gpu(args):
             host_step()
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     h2d = sum(v.numel() * 8 for v in hin.values())
     d2h = sum(v.numel() * 8 for v in hout.values())
 
@@ -288,7 +304,7 @@ def run_gpu(args):
 
     hbm, hbm_src = peaks()
     per_step32 = ms32 / steps
-    value = world * steps / (ms32 * 1e-3)
+    value = whole_job_rate(world, steps, ms32)
     # dominant kernel of the headline form
     dom = max(kt32.items(), key=lambda kv: kv[1][1]) if kt32 else (None, (0, 0.0))
     dname, (dl, dms) = dom
