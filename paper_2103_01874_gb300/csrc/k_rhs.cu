@@ -41,10 +41,13 @@ struct RhsOut {
 
 
 
-// CPT: columns per thread (tj * nx <= CPT * kRhsThreads)
-template <int CPT>
-__global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 1)) k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out,
-                                                           int tj, int kc) {
+// CPT: columns per thread (tj * nx <= CPT * kRhsThreads); RULE: face density
+// rule (0 arithmetic, 1 harmonic); PROJ: the projection's outputs (f as pairs
+// and u_pre, v_pre, w_pre always written, f as FP64 when given) or, with
+// PROJ = false, f as FP64 only (ppe_rhs)
+template <int CPT, int RULE, bool PROJ>
+__global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 1))
+    k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int tj, int kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int ntile = (ny + tj - 1) / tj;
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
   const int j0 = jt * tj, k0 = kci * kc;
   const int steps = min(kc, nz - k0);
   const int nl = tj + 2;  // lines of the current plane held in shared memory (with halos)
-  const int rule = in.face_rule;
+  constexpr int rule = RULE;
 
   // shared: current plane p_hat and rho (nl lines), x-face and y-face values
   df* P = reinterpret_cast<df*>(smem_raw);  // [nl][nx]
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       if (!cv[u]) continue;
       const FaceOut fo = face_q(rl[u], rh[u], pl[u], ph[u], d2df(ws[u]), K.cz, K.gz, K, rule);
       q[u] = fo.q;
-      if (owned && out.wpre) out.wpre[cell(kf, j0 + cj[u], ci[u])] = fo.upre;
+      if (PROJ && owned) out.wpre[cell(kf, j0 + cj[u], ci[u])] = fo.upre;
     }
   };
 
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
         const int i = ci[u], im = (i == 0) ? nx - 1 : i - 1;
         const FaceOut fo = face_q(R[r + im], R[r + i], P[r + im], P[r + i], d2df(us_[u]), K.cx, K.gx, K, rule);
         q = fo.q;
-        if (out.upre) out.upre[cell(k, j0 + cj[u], i)] = fo.upre;
+        if (PROJ) out.upre[cell(k, j0 + cj[u], i)] = fo.upre;
       }
       QX[cj[u] * nx + ci[u]] = q;
     }
@@ -225,14 +228,14 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
             const bool own = (jf < tj) || (j == ny);
             if (j == 0 || j == ny) {
               q = df_norm(df_mulz(K.cy, vs));
-              if (own && out.vpre) out.vpre[cvv] = vs;
+              if (PROJ && own) out.vpre[cvv] = vs;
               wsum = (j == ny) ? df_addz(wsum, vs) : df_subz(wsum, vs);
               wmax = fmaxf(wmax, fabsf(vs.hi));
             } else {
               const int rl = jf * nx + i, rh = (jf + 1) * nx + i;
               const FaceOut fo = face_q(R[rl], R[rh], P[rl], P[rh], vs, K.cy, K.gy, K, rule);
               q = fo.q;
-              if (own && out.vpre) out.vpre[cvv] = fo.upre;
+              if (PROJ && own) out.vpre[cvv] = fo.upre;
             }
           }
           QY[idx] = q;
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       const int r = (cj[u] + 1) * nx + ci[u];
       const FaceOut fo = face_q(R[r], R1[u], P[r], P1[u], d2df(ws_[u]), K.cz, K.gz, K, rule);
       QZup[u] = fo.q;
-      if (k + 1 < k0 + steps && out.wpre) out.wpre[cell(wrapk(k + 1), j0 + cj[u], ci[u])] = fo.upre;
+      if (PROJ && k + 1 < k0 + steps) out.wpre[cell(wrapk(k + 1), j0 + cj[u], ci[u])] = fo.upre;
     }
     __syncthreads();
     // ---- phase B: cells of plane k
@@ -264,8 +267,8 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       const df sv = d2df(ss_[u]);
       const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, sv)));
       smax = fmaxf(smax, fabsf(sv.hi));
-      if (out.fdf) out.fdf[c] = f;
-      if (out.f64) out.f64[c] = df2d(f);
+      if (PROJ) out.fdf[c] = f;
+      if (!PROJ || out.f64) out.f64[c] = df2d(f);
       vmax = fmaxf(vmax, fabsf(f.hi));
       QZ[u] = QZup[u];
     }
@@ -302,12 +305,271 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
 
 __global__ void k_finish_sums(GridDev g, DevScalars* sc) { finish_sums(sc, g); }
 
-size_t rhs_smem(int nx, int tj) {
-  const size_t nl = tj + 2;
-  return sizeof(df) * (2 * nl * nx + (size_t)tj * nx + (size_t)(tj + 1) * nx);
+// Column-stack form of the march for nx <= 256 (the same face and cell
+// arithmetic as k_rhs_march, bit for bit).  The CTA's 256 threads form
+// nstk = 256 / nx stacks; thread (s, i) owns x position i of the S consecutive
+// lines s*S .. s*S + S - 1 of the tile (tile height nstk * S lines).  The own
+// lines' p_hat and rho of the current plane stay in registers, so the thread
+// evaluates the y faces below, between and above its lines from registers
+// (only the line below and the line above its stack come from shared memory,
+// as do the x neighbours), and the y-face values never go through shared
+// memory; the x faces are exchanged through shared memory for the cell
+// divergence.  Faces between two stacks are evaluated by both (same bits).
+template <int S, int RULE, bool PROJ>
+__global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
+    k_rhs_stack(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int kc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nstk = kRhsThreads / nx;
+  const int tj = nstk * S;  // lines per tile
+  const int ntile = (ny + tj - 1) / tj;
+  const int jt = blockIdx.x % ntile, kci = blockIdx.x / ntile;
+  const int j0 = jt * tj, k0 = kci * kc;
+  const int steps = min(kc, nz - k0);
+  const int nl = tj + 2;
+  constexpr int rule = RULE;
+
+  df* P = reinterpret_cast<df*>(smem_raw);  // [nl][nx]: row r holds tile line r - 1
+  df* R = P + nl * nx;                      // [nl][nx]
+  df* QX = R + nl * nx;                     // [tj][nx]
+
+  const StencilConst K = sc->K;
+  const uint32_t plane = (uint32_t)ny * (uint32_t)nx;
+  const uint32_t vplane = (uint32_t)(ny + 1) * (uint32_t)nx;
+
+  const int stk = (int)fdiv((uint32_t)threadIdx.x, g.fd_nx);
+  const int i = (int)threadIdx.x - stk * nx;
+  const bool active = stk < nstk;
+  const int jb = stk * S;                    // first own line (tile coordinates)
+  const int im = (i == 0) ? nx - 1 : i - 1;
+  const int ip = (i + 1 == nx) ? 0 : i + 1;
+  bool cv[S];
+#pragma unroll
+  for (int l = 0; l < S; ++l) cv[l] = active && (j0 + jb + l < ny);
+
+  auto cell = [&](int kk, int j) -> uint32_t { return (uint32_t)kk * plane + (uint32_t)(j * nx + i); };
+  auto wrapk = [&](int kk) { return (kk % nz + nz) % nz; };
+
+  // own lines of plane kk
+  auto load_cols = [&](int kk, df* pv, df* rv) {
+    kk = wrapk(kk);
+    double a[S], b[S], r[S];
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      a[l] = 0.0; b[l] = 0.0; r[l] = 1.0;
+      if (cv[l]) {
+        const uint32_t c = cell(kk, j0 + jb + l);
+        a[l] = __ldg(in.pn + c);
+        b[l] = __ldg(in.pnm1 + c);
+        r[l] = __ldg(in.rho + c);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      pv[l] = df_sub(df_ldexp2(d2df(a[l])), d2df(b[l]));  // p_hat = 2 p^n - p^{n-1}
+      rv[l] = d2df(r[l]);
+    }
+  };
+  // halo lines j0-1 and j0+tj of plane kk into shared rows 0 and nl-1
+  auto load_halo = [&](int kk) {
+    kk = wrapk(kk);
+    for (int idx = threadIdx.x; idx < 2 * nx; idx += kRhsThreads) {
+      const int h = idx >= nx, x = idx - h * nx;
+      const int j = h ? j0 + tj : j0 - 1;
+      const int row = h ? nl - 1 : 0;
+      df pv = {0.0f, 0.0f}, rv = {1.0f, 0.0f};
+      if (j >= 0 && j < ny) {
+        const uint32_t c = (uint32_t)kk * plane + (uint32_t)(j * nx + x);
+        pv = df_sub(df_ldexp2(d2df(__ldg(in.pn + c))), d2df(__ldg(in.pnm1 + c)));
+        rv = d2df(__ldg(in.rho + c));
+      }
+      P[row * nx + x] = pv;
+      R[row * nx + x] = rv;
+    }
+  };
+  auto store_rows = [&](const df* pv, const df* rv) {
+    if (!active) return;
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      P[(jb + l + 1) * nx + i] = pv[l];
+      R[(jb + l + 1) * nx + i] = rv[l];
+    }
+  };
+
+  // raw next-step loads, issued a phase ahead of their use: u*, S of plane k,
+  // w* of face k+1 (own lines), v* of the y faces jb .. jb+S of plane k
+  double us_[S], ss_[S], ws_[S], vs_[S + 1];
+  auto load_step = [&](int k) {
+    const int kw = wrapk(k + 1);
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      us_[l] = cv[l] ? __ldg(in.u + cell(k, j0 + jb + l)) : 0.0;
+      ss_[l] = cv[l] ? __ldg(in.S + cell(k, j0 + jb + l)) : 0.0;
+      ws_[l] = cv[l] ? __ldg(in.w + cell(kw, j0 + jb + l)) : 0.0;
+    }
+#pragma unroll
+    for (int f = 0; f <= S; ++f) {
+      const int j = j0 + jb + f;
+      vs_[f] = (active && j <= ny) ? __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)(j * nx + i))) : 0.0;
+    }
+  };
+
+  df PC[S], RC[S], P1[S], R1[S], QZ[S];
+  // prologue: plane k0 current (registers and shared rows), face k0, plane k0+1 in registers
+  {
+    df Pm[S], Rm[S];
+    load_cols(k0 - 1, Pm, Rm);
+    load_cols(k0, PC, RC);
+    {
+      const int kf = wrapk(k0);
+      double w0[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) w0[l] = cv[l] ? __ldg(in.w + cell(kf, j0 + jb + l)) : 0.0;
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        QZ[l] = {0.0f, 0.0f};
+        if (!cv[l]) continue;
+        const FaceOut fo = face_q(Rm[l], RC[l], Pm[l], PC[l], d2df(w0[l]), K.cz, K.gz, K, rule);
+        QZ[l] = fo.q;
+        if (PROJ) out.wpre[cell(kf, j0 + jb + l)] = fo.upre;
+      }
+    }
+    store_rows(PC, RC);
+    load_halo(k0);
+    load_cols(k0 + 1, P1, R1);
+    load_step(k0);
+  }
+  __syncthreads();
+
+  float vmax = 0.0f, smax = 0.0f, wmax = 0.0f;
+  df wsum = {0.0f, 0.0f};  // wall flux v*(ny) - v*(0) of this CTA's wall faces
+  for (int st = 0; st < steps; ++st) {
+    const int k = k0 + st;
+    const bool more = st + 1 < steps;
+    double rp[S], rm[S], rr[S];
+    if (more) {
+      const int k2 = wrapk(k + 2);
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        rp[l] = 0.0; rm[l] = 0.0; rr[l] = 1.0;
+        if (cv[l]) {
+          const uint32_t c = cell(k2, j0 + jb + l);
+          rp[l] = __ldg(in.pn + c);
+          rm[l] = __ldg(in.pnm1 + c);
+          rr[l] = __ldg(in.rho + c);
+        }
+      }
+    }
+    // ---- phase A: x faces (shared x neighbour), y faces and the upper z face (registers)
+    df QXo[S], QY[S + 1], QZup[S];
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      QXo[l] = {0.0f, 0.0f};
+      if (!cv[l]) continue;
+      const int r = (jb + l + 1) * nx;
+      const FaceOut fo = face_q(R[r + im], RC[l], P[r + im], PC[l], d2df(us_[l]), K.cx, K.gx, K, rule);
+      QXo[l] = fo.q;
+      if (PROJ) out.upre[cell(k, j0 + jb + l)] = fo.upre;
+    }
+    if (active) {
+#pragma unroll
+      for (int l = 0; l < S; ++l) QX[(jb + l) * nx + i] = QXo[l];
+    }
+#pragma unroll
+    for (int f = 0; f <= S; ++f) {  // face between tile lines jb+f-1 and jb+f
+      QY[f] = {0.0f, 0.0f};
+      const int j = j0 + jb + f;
+      if (!active || j > ny) continue;
+      const df vs = d2df(vs_[f]);
+      const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
+      // a face belongs to the stack holding the line above it; the top wall to
+      // the stack holding line ny - 1
+      const bool own = (f < S && j < ny) || (j == ny && f >= 1);
+      if (j == 0 || j == ny) {
+        QY[f] = df_norm(df_mulz(K.cy, vs));
+        if (PROJ && own) out.vpre[cvv] = vs;
+        if (own) {
+          wsum = (j == ny) ? df_addz(wsum, vs) : df_subz(wsum, vs);
+          wmax = fmaxf(wmax, fabsf(vs.hi));
+        }
+      } else {
+        const df rl = (f == 0) ? R[(jb) * nx + i] : RC[f > 0 ? f - 1 : 0];
+        const df pl = (f == 0) ? P[(jb) * nx + i] : PC[f > 0 ? f - 1 : 0];
+        const df rh = (f == S) ? R[(jb + S + 1) * nx + i] : RC[f < S ? f : 0];
+        const df ph = (f == S) ? P[(jb + S + 1) * nx + i] : PC[f < S ? f : 0];
+        const FaceOut fo = face_q(rl, rh, pl, ph, vs, K.cy, K.gy, K, rule);
+        QY[f] = fo.q;
+        if (PROJ && own) out.vpre[cvv] = fo.upre;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      QZup[l] = {0.0f, 0.0f};
+      if (!cv[l]) continue;
+      const FaceOut fo = face_q(RC[l], R1[l], PC[l], P1[l], d2df(ws_[l]), K.cz, K.gz, K, rule);
+      QZup[l] = fo.q;
+      if (PROJ && k + 1 < k0 + steps) out.wpre[cell(wrapk(k + 1), j0 + jb + l)] = fo.upre;
+    }
+    __syncthreads();
+    // ---- phase B: cells of plane k
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      if (!cv[l]) continue;
+      // f = sum over directions of (Q~_+ - Q~_-) / h^2 - (rho_0/dt) S
+      const df dxq = df_mulz(df_subz(QX[(jb + l) * nx + ip], QXo[l]), K.lx);
+      const df dyq = df_mulz(df_subz(QY[l + 1], QY[l]), K.ly);
+      const df dzq = df_mulz(df_subz(QZup[l], QZ[l]), K.lz);
+      const uint32_t c = cell(k, j0 + jb + l);
+      const df sv = d2df(ss_[l]);
+      const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, sv)));
+      smax = fmaxf(smax, fabsf(sv.hi));
+      if (PROJ) out.fdf[c] = f;
+      if (!PROJ || out.f64) out.f64[c] = df2d(f);
+      vmax = fmaxf(vmax, fabsf(f.hi));
+      QZ[l] = QZup[l];
+    }
+    if (more) {
+      load_step(k + 1);
+      // ---- phase C: plane k+1 becomes current; plane k+2 (loaded above) into
+      // registers.  Phase B reads only QX, so the rows can be rewritten without
+      // a barrier; the barrier below orders them before the next phase A.
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        PC[l] = P1[l];
+        RC[l] = R1[l];
+      }
+      store_rows(PC, RC);
+      load_halo(k + 1);
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        P1[l] = df_sub(df_ldexp2(d2df(rp[l])), d2df(rm[l]));
+        R1[l] = d2df(rr[l]);
+      }
+      __syncthreads();
+    }
+  }
+  block_max_to(&sc->fmax_bits, vmax);
+  block_max_to(&sc->smax_bits, smax);
+  block_max_to(&sc->wallv_bits, wmax);
+  if (j0 == 0 || j0 + tj >= ny) block_pair_sums(wsum, df{0.0f, 0.0f}, sc->part + blockIdx.x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rhs_tiles = ntile;
+    sc->rhs_chunks = (nz + kc - 1) / kc;
+  }
+}
+
+// Lines per tile: the stack form (nx <= 256) has 256 / nx stacks of `lines`
+// lines each; the general form has `lines` lines.
+int rhs_tile_lines(int nx, int lines) { return nx <= kRhsThreads ? (kRhsThreads / nx) * lines : lines; }
+
+size_t rhs_smem(int nx, int lines) {
+  const size_t tj = rhs_tile_lines(nx, lines), nl = tj + 2;
+  if (nx <= kRhsThreads) return sizeof(df) * (2 * nl * nx + tj * nx);
+  return sizeof(df) * (2 * nl * nx + tj * nx + (tj + 1) * nx);
 }
 
 int rhs_max_lines(int nx) {
+  if (nx <= kRhsThreads) return kRhsMaxCols;
   int tj = 8;
   while (tj > 1 && tj * nx > kRhsThreads * kRhsMaxCols) tj /= 2;
   return tj;
@@ -321,19 +583,49 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
   o.upre = upre;
   o.vpre = vpre;
   o.wpre = wpre;
-  const int ntile = (g.ny + tj - 1) / tj;
+  const int tile = rhs_tile_lines(g.nx, tj);
+  const int ntile = (g.ny + tile - 1) / tile;
   const int nchunk = (g.nz + kc - 1) / kc;
-  const int ncol = tj * g.nx;
   const size_t sm = rhs_smem(g.nx, tj);
   const int grid = ntile * nchunk;
-  if (ncol <= kRhsThreads)
-    k_rhs_march<1><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
-  else if (ncol <= 2 * kRhsThreads)
-    k_rhs_march<2><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
-  else if (ncol <= 4 * kRhsThreads)
-    k_rhs_march<4><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
-  else
-    k_rhs_march<8><<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc);
+  const bool proj = fdf != nullptr;
+  if (proj && !(upre && vpre && wpre)) return cudaErrorInvalidValue;
+  if (!proj && !f64) return cudaErrorInvalidValue;
+  if (g.nx <= kRhsThreads) {
+    // column-stack form: tj is the stack height S
+    auto go = [&](auto kernel) { kernel<<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, kc); };
+#define PPE_STACK_CASE(C)                                                        \
+    if (tj == C) {                                                               \
+      if (in.face_rule == 0) {                                                   \
+        if (proj) go(k_rhs_stack<C, 0, true>); else go(k_rhs_stack<C, 0, false>); \
+      } else {                                                                   \
+        if (proj) go(k_rhs_stack<C, 1, true>); else go(k_rhs_stack<C, 1, false>); \
+      }                                                                          \
+    }
+    PPE_STACK_CASE(1)
+    PPE_STACK_CASE(2)
+    PPE_STACK_CASE(4)
+    PPE_STACK_CASE(8)
+#undef PPE_STACK_CASE
+    return cudaGetLastError();
+  }
+  const int ncol = tj * g.nx;
+  const int cpt = ncol <= kRhsThreads ? 1 : ncol <= 2 * kRhsThreads ? 2 : ncol <= 4 * kRhsThreads ? 4 : 8;
+  auto go = [&](auto kernel) { kernel<<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc); };
+  // instance table: [cpt][rule][proj]
+#define PPE_RHS_CASE(C)                                                        \
+  if (cpt == C) {                                                              \
+    if (in.face_rule == 0) {                                                   \
+      if (proj) go(k_rhs_march<C, 0, true>); else go(k_rhs_march<C, 0, false>); \
+    } else {                                                                   \
+      if (proj) go(k_rhs_march<C, 1, true>); else go(k_rhs_march<C, 1, false>); \
+    }                                                                          \
+  }
+  PPE_RHS_CASE(1)
+  PPE_RHS_CASE(2)
+  PPE_RHS_CASE(4)
+  PPE_RHS_CASE(8)
+#undef PPE_RHS_CASE
   return cudaGetLastError();
 }
 
@@ -356,22 +648,33 @@ cudaError_t launch_finish_sums(const GridDev& g, DevScalars* sc, cudaStream_t st
   return cudaGetLastError();
 }
 
+template <int C>
+cudaError_t raise_rhs(size_t* cap) {
+  cudaError_t e = raise_smem(k_rhs_march<C, 0, true>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<C, 0, false>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<C, 1, true>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_march<C, 1, false>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_stack<C, 0, true>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_stack<C, 0, false>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_stack<C, 1, true>, cap);
+  if (e == cudaSuccess) e = raise_smem(k_rhs_stack<C, 1, false>, cap);
+  return e;
+}
+
 cudaError_t set_rhs_smem_limit() {
   size_t cap = kSmemPerCta;
-  cudaError_t e = raise_smem(k_rhs_march<1>, &cap);
-  if (e == cudaSuccess) e = raise_smem(k_rhs_march<2>, &cap);
-  if (e == cudaSuccess) e = raise_smem(k_rhs_march<4>, &cap);
-  if (e == cudaSuccess) e = raise_smem(k_rhs_march<8>, &cap);
+  cudaError_t e = raise_rhs<1>(&cap);
+  if (e == cudaSuccess) e = raise_rhs<2>(&cap);
+  if (e == cudaSuccess) e = raise_rhs<4>(&cap);
+  if (e == cudaSuccess) e = raise_rhs<8>(&cap);
   return e;
 }
 
 size_t rhs_smem_limit() {
   size_t cap = kSmemPerCta;
-  if (set_rhs_smem_limit() != cudaSuccess) return 0;
-  raise_smem(k_rhs_march<1>, &cap);
-  raise_smem(k_rhs_march<2>, &cap);
-  raise_smem(k_rhs_march<4>, &cap);
-  raise_smem(k_rhs_march<8>, &cap);
+  if (raise_rhs<1>(&cap) != cudaSuccess || raise_rhs<2>(&cap) != cudaSuccess || raise_rhs<4>(&cap) != cudaSuccess ||
+      raise_rhs<8>(&cap) != cudaSuccess)
+    return 0;
   return cap;
 }
 

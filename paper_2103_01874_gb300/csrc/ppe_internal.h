@@ -90,8 +90,8 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
 // Totals of the per-CTA partial sums into sc (one CTA, finish_sums); the first
 // forward z pass after an x transform of f does the same in its CTA 0.
 cudaError_t launch_finish_sums(const GridDev& g, DevScalars* sc, cudaStream_t st);
-size_t rhs_smem(int nx, int tj);
-int rhs_max_lines(int nx);  // tj * nx may not exceed the columns the threads of a CTA hold
+size_t rhs_smem(int nx, int lines);  // dynamic shared memory of the RHS kernel for a rhs_lines value
+int rhs_max_lines(int nx);  // largest rhs_lines value (lines per thread stack, or per tile when nx > 256)
 cudaError_t set_rhs_smem_limit();
 size_t rhs_smem_limit();  // largest dynamic shared memory every k_rhs_march instance accepts
 constexpr size_t kSmemPerCta = 227 * 1024;  // opt-in shared memory per CTA (static + dynamic)
