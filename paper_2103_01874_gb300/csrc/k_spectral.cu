@@ -160,17 +160,19 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         const int line = l0 + ll;
         jj[u] = -1;
         if (idx < lpb * nx && line < nlines) {
-          const int k = (int)fdiv(line, g.fd_ny), j = line - k * g.ny;
-          jj[u] = j;
-          const Nbr n = neighbours(g, i, j, k);
-          pc[u] = pdf[n.c];
-          pxp[u] = pdf[n.xp];
-          pxm[u] = pdf[n.xm];
-          pzp[u] = pdf[n.zp];
-          pzm[u] = pdf[n.zm];
-          pyp[u] = (j + 1 < g.ny) ? pdf[n.c + nx] : pc[u];
-          pym[u] = (j > 0) ? pdf[n.c - nx] : pc[u];
-          fv[u] = fdf[n.c];
+          // 32-bit offsets (grids up to 1024^3)
+          const uint32_t k = fdiv((uint32_t)line, g.fd_ny), j = (uint32_t)line - k * (uint32_t)g.ny;
+          const uint32_t plane = (uint32_t)g.ny * (uint32_t)nx, nzu = (uint32_t)g.nz;
+          const uint32_t c = (uint32_t)line * (uint32_t)nx + (uint32_t)i;
+          jj[u] = (int)j;
+          pc[u] = pdf[c];
+          pxp[u] = pdf[(i + 1 == nx) ? c + 1 - nx : c + 1];
+          pxm[u] = pdf[(i == 0) ? c + nx - 1 : c - 1];
+          pzp[u] = pdf[(k + 1 == nzu) ? c - (nzu - 1) * plane : c + plane];
+          pzm[u] = pdf[(k == 0) ? c + (nzu - 1) * plane : c - plane];
+          pyp[u] = (j + 1 < (uint32_t)g.ny) ? pdf[c + nx] : pc[u];
+          pym[u] = (j > 0) ? pdf[c - nx] : pc[u];
+          fv[u] = fdf[c];
         }
       }
 #pragma unroll
@@ -179,10 +181,11 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         if (idx >= lpb * nx) continue;
         T val = (T)0;
         if (jj[u] >= 0) {
-          const df p0 = pc[u];
-          const df lx = df_subz(df_subz(pxp[u], p0), df_subz(p0, pxm[u]));
-          const df lz = df_subz(df_subz(pzp[u], p0), df_subz(p0, pzm[u]));
-          const df ly = df_subz(df_subz(pyp[u], p0), df_subz(p0, pym[u]));  // wall sides contribute 0
+          // second differences as (p+ + p-) - 2 p (the wall sides contribute 0)
+          const df p2 = df_ldexp2(pc[u]);
+          const df lx = df_subz(df_addz(pxp[u], pxm[u]), p2);
+          const df lz = df_subz(df_addz(pzp[u], pzm[u]), p2);
+          const df ly = df_subz(df_addz(pyp[u], pym[u]), p2);
           const df lap = df_addz(df_addz(df_mulz(lx, lc[0]), df_mulz(ly, lc[1])), df_mulz(lz, lc[2]));
           const float r = df_to_f(df_subz(df_subz(fv[u], fmean), lap));
           val = (T)r;

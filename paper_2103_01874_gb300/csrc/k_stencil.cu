@@ -207,8 +207,10 @@ __device__ __forceinline__ void correct_check_body(const GridDev& g, const df* _
                                                    const df* __restrict__ vpre, const df* __restrict__ wpre,
                                                    const df* __restrict__ pdf, const df* __restrict__ fdf,
                                                    DevScalars* sc, df fmean) {
-  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
-  const uint32_t total = (uint32_t)g.nz * (ny + 1) * nx;
+  // 32-bit offsets: grids up to 1024^3 (v: nx (ny+1) nz < 2^32)
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, nz = (uint32_t)g.nz;
+  const uint32_t plane = ny * nx;
+  const uint32_t total = nz * (ny + 1) * nx;
   const StencilConst K = sc->K;
   double* const u_out = sc->out_u;
   double* const v_out = sc->out_v;
@@ -216,61 +218,40 @@ __device__ __forceinline__ void correct_check_body(const GridDev& g, const df* _
   double* const p_out = sc->out_p;
   const int slot = sc->iter + 1;
   float vmax = 0.0f;
-  constexpr int U = 1;  // one face per thread and round: 4 CTAs per SM fit the register budget
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
-    df vp[U], up[U], wp[U], p0[U], pym[U], pxm[U], pzm[U], pyp[U], pxp[U], pzp[U], fv[U];
-    size_t cc[U];
-    int jj[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t t = t0 + u * stride;
-      jj[u] = -1;
-      if (t >= total) continue;
-      const uint32_t r = fdiv(t, g.fd_nx);
-      const int i = (int)(t - r * nx);
-      const int k = (int)fdiv(r, g.fd_nyp1);
-      const int j = (int)(r - (uint32_t)k * (ny + 1));
-      jj[u] = j;
-      vp[u] = vpre[t];
-      if (j < (int)ny) {
-        const Nbr n = neighbours(g, i, j, k);
-        cc[u] = n.c;
-        up[u] = upre[n.c];
-        wp[u] = wpre[n.c];
-        p0[u] = pdf[n.c];
-        pxm[u] = pdf[n.xm];
-        pzm[u] = pdf[n.zm];
-        pxp[u] = pdf[n.xp];
-        pzp[u] = pdf[n.zp];
-        pym[u] = (j > 0) ? pdf[n.c - nx] : p0[u];
-        pyp[u] = (j + 1 < (int)ny) ? pdf[n.c + nx] : p0[u];
-        fv[u] = fdf[n.c];
-      }
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    // t indexes the v faces [k][j][i], j = 0..ny; j < ny also carries cell (i, j, k)
+    const uint32_t r = fdiv(t, g.fd_nx);
+    const uint32_t i = t - r * nx;
+    const uint32_t k = fdiv(r, g.fd_nyp1);
+    const uint32_t j = r - k * (ny + 1);
+    const df vp = vpre[t];
+    if (j == ny) {  // upper wall: v unchanged
+      v_out[t] = df2d(vp);
+      continue;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = jj[u];
-      if (j < 0) continue;
-      const uint32_t t = t0 + u * stride;
-      if (j == 0 || j == (int)ny) {
-        v_out[t] = df2d(vp[u]);
-        if (j == (int)ny) continue;
-      } else {
-        v_out[t] = df2d(df_subz(vp[u], df_mulz(K.gy, df_subz(p0[u], pym[u]))));
-      }
-      const size_t c = cc[u];
-      const df q = p0[u];
-      u_out[c] = df2d(df_subz(up[u], df_mulz(K.gx, df_subz(q, pxm[u]))));
-      w_out[c] = df2d(df_subz(wp[u], df_mulz(K.gz, df_subz(q, pzm[u]))));
-      p_out[c] = df2d(q);
-      const df lx = df_subz(df_subz(pxp[u], q), df_subz(q, pxm[u]));
-      const df ly = df_subz(df_subz(pyp[u], q), df_subz(q, pym[u]));
-      const df lz = df_subz(df_subz(pzp[u], q), df_subz(q, pzm[u]));
-      const df lap = df_addz(df_addz(df_mulz(lx, K.lx), df_mulz(ly, K.ly)), df_mulz(lz, K.lz));
-      const df fr = SUB ? df_subz(fv[u], fmean) : fv[u];
-      vmax = fmaxf(vmax, fabsf(df_to_f(df_subz(fr, lap))));
-    }
+    const uint32_t c = k * plane + j * nx + i;
+    const uint32_t xm = (i == 0) ? c + nx - 1 : c - 1;
+    const uint32_t xp = (i + 1 == nx) ? c + 1 - nx : c + 1;
+    const uint32_t zm = (k == 0) ? c + (nz - 1) * plane : c - plane;
+    const uint32_t zp = (k + 1 == nz) ? c - (nz - 1) * plane : c + plane;
+    const df up = upre[c], wp = wpre[c], q = pdf[c];
+    const df pxm = pdf[xm], pxp = pdf[xp], pzm = pdf[zm], pzp = pdf[zp];
+    const df pym = (j > 0) ? pdf[c - nx] : q;
+    const df pyp = (j + 1 < ny) ? pdf[c + nx] : q;
+    const df fv = fdf[c];
+    // backward differences (the faces of this cell) serve Eq. (33) and the residual
+    const df dxm = df_subz(q, pxm), dym = df_subz(q, pym), dzm = df_subz(q, pzm);
+    v_out[t] = df2d(j == 0 ? vp : df_subz(vp, df_mulz(K.gy, dym)));  // lower wall: v unchanged
+    u_out[c] = df2d(df_subz(up, df_mulz(K.gx, dxm)));
+    w_out[c] = df2d(df_subz(wp, df_mulz(K.gz, dzm)));
+    p_out[c] = df2d(q);
+    const df lx = df_subz(df_subz(pxp, q), dxm);
+    const df ly = df_subz(df_subz(pyp, q), dym);
+    const df lz = df_subz(df_subz(pzp, q), dzm);
+    const df lap = df_addz(df_addz(df_mulz(lx, K.lx), df_mulz(ly, K.ly)), df_mulz(lz, K.lz));
+    const df fr = SUB ? df_subz(fv, fmean) : fv;
+    vmax = fmaxf(vmax, fabsf(df_to_f(df_subz(fr, lap))));
   }
   block_max_to(&sc->rmax_bits[slot], vmax);
 }
