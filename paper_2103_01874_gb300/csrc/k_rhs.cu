@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
   df P1[CPT], R1[CPT], QZ[CPT];
 
   auto cell = [&](int kk, int j, int i) -> uint32_t { return (uint32_t)kk * plane + (uint32_t)(j * nx + i); };
-  auto wrapk = [&](int kk) { return (kk % nz + nz) % nz; };
+  auto wrapk = [&](int kk) { return kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk); };  // kk in [-nz, 2 nz)
 
   // own columns of plane kk into (pv, rv)
   auto load_cols = [&](int kk, df* pv, df* rv) {
@@ -348,7 +348,11 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
   for (int l = 0; l < S; ++l) cv[l] = active && (j0 + jb + l < ny);
 
   auto cell = [&](int kk, int j) -> uint32_t { return (uint32_t)kk * plane + (uint32_t)(j * nx + i); };
-  auto wrapk = [&](int kk) { return (kk % nz + nz) % nz; };
+  uint32_t coff[S];  // offsets of the own lines within a plane
+#pragma unroll
+  for (int l = 0; l < S; ++l) coff[l] = (uint32_t)((j0 + jb + l) * nx + i);
+  auto cellL = [&](int kk, int l) -> uint32_t { return (uint32_t)kk * plane + coff[l]; };
+  auto wrapk = [&](int kk) { return kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk); };  // kk in [-nz, 2 nz)
 
   // own lines of plane kk
   auto load_cols = [&](int kk, df* pv, df* rv) {
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     for (int l = 0; l < S; ++l) {
       a[l] = 0.0; b[l] = 0.0; r[l] = 1.0;
       if (cv[l]) {
-        const uint32_t c = cell(kk, j0 + jb + l);
+        const uint32_t c = cellL(kk, l);
         a[l] = __ldg(in.pn + c);
         b[l] = __ldg(in.pnm1 + c);
         r[l] = __ldg(in.rho + c);
@@ -403,9 +407,9 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     const int kw = wrapk(k + 1);
 #pragma unroll
     for (int l = 0; l < S; ++l) {
-      us_[l] = cv[l] ? __ldg(in.u + cell(k, j0 + jb + l)) : 0.0;
-      ss_[l] = cv[l] ? __ldg(in.S + cell(k, j0 + jb + l)) : 0.0;
-      ws_[l] = cv[l] ? __ldg(in.w + cell(kw, j0 + jb + l)) : 0.0;
+      us_[l] = cv[l] ? __ldg(in.u + cellL(k, l)) : 0.0;
+      ss_[l] = cv[l] ? __ldg(in.S + cellL(k, l)) : 0.0;
+      ws_[l] = cv[l] ? __ldg(in.w + cellL(kw, l)) : 0.0;
     }
 #pragma unroll
     for (int f = 0; f <= S; ++f) {
@@ -424,14 +428,14 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       const int kf = wrapk(k0);
       double w0[S];
 #pragma unroll
-      for (int l = 0; l < S; ++l) w0[l] = cv[l] ? __ldg(in.w + cell(kf, j0 + jb + l)) : 0.0;
+      for (int l = 0; l < S; ++l) w0[l] = cv[l] ? __ldg(in.w + cellL(kf, l)) : 0.0;
 #pragma unroll
       for (int l = 0; l < S; ++l) {
         QZ[l] = {0.0f, 0.0f};
         if (!cv[l]) continue;
         const FaceOut fo = face_q(Rm[l], RC[l], Pm[l], PC[l], d2df(w0[l]), K.cz, K.gz, K, rule);
         QZ[l] = fo.q;
-        if (PROJ) out.wpre[cell(kf, j0 + jb + l)] = fo.upre;
+        if (PROJ) out.wpre[cellL(kf, l)] = fo.upre;
       }
     }
     store_rows(PC, RC);
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       for (int l = 0; l < S; ++l) {
         rp[l] = 0.0; rm[l] = 0.0; rr[l] = 1.0;
         if (cv[l]) {
-          const uint32_t c = cell(k2, j0 + jb + l);
+          const uint32_t c = cellL(k2, l);
           rp[l] = __ldg(in.pn + c);
           rm[l] = __ldg(in.pnm1 + c);
           rr[l] = __ldg(in.rho + c);
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       const int r = (jb + l + 1) * nx;
       const FaceOut fo = face_q(R[r + im], RC[l], P[r + im], PC[l], d2df(us_[l]), K.cx, K.gx, K, rule);
       QXo[l] = fo.q;
-      if (PROJ) out.upre[cell(k, j0 + jb + l)] = fo.upre;
+      if (PROJ) out.upre[cellL(k, l)] = fo.upre;
     }
     if (active) {
 #pragma unroll
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       if (!cv[l]) continue;
       const FaceOut fo = face_q(RC[l], R1[l], PC[l], P1[l], d2df(ws_[l]), K.cz, K.gz, K, rule);
       QZup[l] = fo.q;
-      if (PROJ && k + 1 < k0 + steps) out.wpre[cell(wrapk(k + 1), j0 + jb + l)] = fo.upre;
+      if (PROJ && k + 1 < k0 + steps) out.wpre[cellL(wrapk(k + 1), l)] = fo.upre;
     }
     __syncthreads();
     // ---- phase B: cells of plane k
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       const df dxq = df_mulz(df_subz(QX[(jb + l) * nx + ip], QXo[l]), K.lx);
       const df dyq = df_mulz(df_subz(QY[l + 1], QY[l]), K.ly);
       const df dzq = df_mulz(df_subz(QZup[l], QZ[l]), K.lz);
-      const uint32_t c = cell(k, j0 + jb + l);
+      const uint32_t c = cellL(k, l);
       const df sv = d2df(ss_[l]);
       const df f = df_norm(df_subz(df_addz(df_addz(dxq, dyq), dzq), df_mulz(K.c, sv)));
       smax = fmaxf(smax, fabsf(sv.hi));
