@@ -41,10 +41,13 @@ F_BYTES = 8 * N_CELLS
 
 def set_grid(n: int):
     """Grid edge for profiling runs of a smaller case (the bench line itself is 256^3)."""
-    global NX, NY, NZ, N_CELLS, F_BYTES
+    global NX, NY, NZ, N_CELLS, F_BYTES, WORKLOAD
     NX = NY = NZ = n
     N_CELLS = n ** 3
     F_BYTES = 8 * N_CELLS
+    if n != 256:
+        WORKLOAD = (f"multimode {n}x{n}x{n} (profiling case), density 640/60, FP32 solve + FP64 refinement "
+                    f"to rel residual 1e-10")
 
 
 def peaks():
@@ -342,7 +345,8 @@ def run_gpu(args):
         "data": "synthetic (seeded two-phase fields, numpy default_rng)",
         "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "precision": "fp32+fp64-refine",
                    "refine_tol": 1e-10, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs 0.94 GB > L2 (no flush needed)"},
+                   "l2": f"inputs {7 * F_BYTES / 1e9:.2f} GB > L2 (no flush needed)" if 7 * F_BYTES > 135e6
+                   else "inputs smaller than L2"},
         "gpts_per_s": value * N_CELLS / 1e9,
         "sweeps": sweeps,
         "rel_residual": info32.rel_residual,
