@@ -254,6 +254,37 @@ def var_coeff_solve_dense(rhs, rho, lengths, rule=FACE_ARITHMETIC):
     return dense_zero_mean_solve(mat, rhs)
 
 
+def unsplit_rhs(u, v, w, S, dt, lengths):
+    """Right side of Eq. (30): (D u* - S) / dt."""
+    h = spacings(S.shape, lengths)
+    return (div(u, v, w, h) - S) / dt
+
+
+def unsplit_correct(u, v, w, rho, p, dt, lengths, rule=FACE_ARITHMETIC):
+    """u^{n+1} = u* - dt G p / rho_f on every face, Eq. (29) (G = 0 on the walls)."""
+    h = spacings(rho.shape, lengths)
+    gx, gy, gz = grad(p, h)
+    rx, ry, rz = face_density(rho, rule)
+    return u - dt * gx / rx, v - dt * gy / ry, w - dt * gz / rz
+
+
+def unsplit_project_dense(u, v, w, S, rho, dt, lengths, rule=FACE_ARITHMETIC):
+    """The unsplit projection, Eqs. (29)-(30), with the variable-coefficient
+    equation solved exactly by dense LU (zero-mean p): small grids only.
+    Returns dict(g, p, u, v, w), g the right side of Eq. (30)."""
+    g = unsplit_rhs(u, v, w, S, dt, lengths)
+    p = var_coeff_solve_dense(g, rho, lengths, rule)
+    u1, v1, w1 = unsplit_correct(u, v, w, rho, p, dt, lengths, rule)
+    return dict(g=g, p=p, u=u1, v=v1, w=w1)
+
+
+def unsplit_residual(p, g, rho, lengths, rule=FACE_ARITHMETIC):
+    """||(g - mean g) - A p||_inf / ||g - mean g||_inf for Eq. (30)."""
+    gc = g - g.mean()
+    r = gc - var_coeff_apply(p, rho, lengths, rule)
+    return float(np.max(np.abs(r)) / np.max(np.abs(gc)))
+
+
 def rel_linf(a, b):
     """max|a - b| / max|b|."""
     a = np.asarray(a)
