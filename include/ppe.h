@@ -172,6 +172,26 @@ ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
  * ppe_get_info does. */
 ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
 
+/* The unsplit projection, Eqs. (29)-(30) -- the iterative baseline that the
+ * split method replaces.  The variable-coefficient equation
+ *   D[(1/rho_f) G p] = (D u* - S) / dt
+ * (rho_f by the plan's face rule, walls as in ppe_project) is solved by
+ * conjugate gradients preconditioned with this plan's constant-coefficient FFT
+ * solve (FP32 or FP64 by the plan's precision; the Polak-Ribiere update keeps
+ * CG convergent with the FP32 preconditioner), starting from p = 0 and
+ * stopping when max|r - mean r| <= tol max|g| (g the right side) or after
+ * max_iter iterations; then u^{n+1} = u* - dt G p / rho_f (Eq. (29)).
+ * Uses fields->u, v, w, S, rho, dt and writes p (zero mean), u_out, v_out,
+ * w_out; p_n, p_nm1, rho0 and f are ignored.  Vectors and the operator are
+ * evaluated in float pairs (~48 bits).  The plan allocates 64 bytes per cell
+ * on the first call.  Asynchronous on the plan's stream; not capturable
+ * (PPE_ERR_INVALID_ARG if the stream is capturing).  tol >= 0,
+ * 0 <= max_iter <= 100000. */
+ppe_status ppe_project_unsplit(ppe_plan_t plan, const ppe_fields* fields, double tol, int max_iter);
+/* Synchronise and read the last unsplit projection's iteration count and
+ * relative residual; PPE_ERR_NOT_CONVERGED if it stopped above its tolerance. */
+ppe_status ppe_unsplit_info(ppe_plan_t plan, int* iterations, double* rel_residual);
+
 /* Batched projections (many grids of any sizes in one launch).  Each plan
  * (distinct; a plan may appear once per batch) is paired with its fields.
  * ppe_batch_create captures the projections once into a CUDA graph whose

@@ -49,6 +49,11 @@ struct ppe_plan_s {
   // ppe_solve's and ppe_project's (the latter ends with the fused correction)
   cudaGraphExec_t refine_exec;
   cudaGraphExec_t project_exec;
+  // unsplit projection (ppe_project_unsplit; allocated on first use): face
+  // coefficients, CG vectors, partial sums, the iteration graph
+  df* vc[8];          // ax, ay, az, x, r, p, Kp, zs
+  double2* pcg_part;
+  cudaGraphExec_t pcg_exec;
   // ppe_project_host staging (allocated on first use)
   double* io[12];
   size_t workspace;
@@ -251,11 +256,13 @@ ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_E
 
 // Kernel names reported by ppe_profile_read.
 enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
-                K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_COUNT };
+                K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_VC_SETUP, K_VC_APPLY, K_VC_UPDATE,
+                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
                                            "k_xfwd_resid", "k_zfft_fwd", "k_ysolve", "k_zfft_inv",
                                            "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
-                                           "k_df_to_d"};
+                                           "k_df_to_d", "k_vc_setup", "k_vc_apply", "k_vc_update",
+                                           "k_vc_dots", "k_vc_pupdate", "k_vc_scalars", "k_vc_correct"};
 constexpr int kProfMax = 16384;
 
 int prof_begin(ppe_plan_t P, int id) {
@@ -473,6 +480,113 @@ ppe_status build_refine_graphs(ppe_plan_t P) {
   return s;
 }
 
+// ---- unsplit projection (Eqs. (29)-(30)) by preconditioned conjugate gradients ----
+enum { VC_AX, VC_AY, VC_AZ, VC_X, VC_R, VC_P, VC_KP, VC_ZS };
+
+ppe_status ensure_vc(ppe_plan_t P) {
+  const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
+  for (int i = 0; i < 8; ++i)
+    if (!P->vc[i]) {
+      ppe_status s = alloc_status(cudaMalloc((void**)&P->vc[i], sizeof(df) * n));
+      if (s != PPE_OK) return s;
+    }
+  if (!P->pcg_part) return alloc_status(cudaMalloc((void**)&P->pcg_part, sizeof(double2) * vc_grid(n)));
+  return PPE_OK;
+}
+
+VcConst make_vc_const(const ppe_grid& g, double dt) {
+  const double hx = g.lx / g.nx, hy = g.ly / g.ny, hz = g.lz / g.nz;
+  VcConst C;
+  C.ix2 = d2df(1.0 / (hx * hx));
+  C.iy2 = d2df(1.0 / (hy * hy));
+  C.iz2 = d2df(1.0 / (hz * hz));
+  C.idx = d2df(1.0 / hx);
+  C.idy = d2df(1.0 / hy);
+  C.idz = d2df(1.0 / hz);
+  C.idt = d2df(1.0 / dt);
+  C.dthx = d2df(dt * hx);
+  C.dthy = d2df(dt * hy);
+  C.dthz = d2df(dt * hz);
+  return C;
+}
+
+// zs = L^{-1} r by the plan's FFT solve (the preconditioner is z = -zs)
+ppe_status vc_precond(ppe_plan_t P) {
+  StencilIn in;
+  memset(&in, 0, sizeof(in));
+  df* r = P->vc[VC_R];
+  df* zs = P->vc[VC_ZS];
+  if (P->fp32) {
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<float>*)P->spec,
+                                               P->rp_half, (const cpx<float>*)P->tw_x, P->lpb, P->stream));
+    return solve_tail<float>(P, XI_DF, nullptr, zs, false);
+  }
+  PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<double>*)P->spec,
+                                              P->rp_half, (const cpx<double>*)P->tw_x, P->lpb, P->stream));
+  return solve_tail<double>(P, XI_DF, nullptr, zs, false);
+}
+
+// One iteration: Kp, alpha, x and r, z = M^{-1} r, beta and the test, p.
+ppe_status vc_iteration(ppe_plan_t P, cudaGraphConditionalHandle h, int use_handle) {
+  df** V = P->vc;
+  PPE_LAUNCH(P, K_VC_APPLY, launch_vc_apply(P->gd, V[VC_P], V[VC_AX], V[VC_AY], V[VC_AZ], V[VC_KP], P->pcg_part,
+                                            P->stream));
+  PPE_LAUNCH(P, K_VC_SCALAR, launch_vc_alpha(P->gd, P->sc, P->pcg_part, P->stream));
+  PPE_LAUNCH(P, K_VC_UPDATE, launch_vc_update(P->gd, V[VC_X], V[VC_R], V[VC_P], V[VC_KP], P->sc, P->stream));
+  ppe_status s = vc_precond(P);
+  if (s != PPE_OK) return s;
+  PPE_LAUNCH(P, K_VC_DOTS, launch_vc_dots(P->gd, V[VC_R], V[VC_ZS], V[VC_KP], P->pcg_part, P->stream));
+  PPE_LAUNCH(P, K_VC_SCALAR, launch_vc_beta(P->gd, P->sc, P->pcg_part, 0, h, use_handle, P->stream));
+  PPE_LAUNCH(P, K_VC_PUPDATE, launch_vc_pupdate(P->gd, V[VC_P], V[VC_ZS], P->sc, P->stream));
+  return PPE_OK;
+}
+
+// The iteration loop as a graph: WHILE(cond) { iteration }, the condition
+// (default 1) set on the device by the beta kernel.  Built once per plan; it
+// touches plan-owned buffers and the device scalar block only.
+ppe_status build_pcg_graph(ppe_plan_t P) {
+  const int saved_prof = P->prof_on;
+  cudaStream_t saved = P->stream;
+  cudaStream_t cs = nullptr, bs = nullptr;
+  cudaGraph_t g = nullptr;
+  auto fail = [&](ppe_status s) {
+    P->stream = saved;
+    P->prof_on = saved_prof;
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (bs) cudaStreamDestroy(bs);
+    cudaGetLastError();
+    return s;
+  };
+  P->prof_on = 0;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(PPE_ERR_CUDA);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond = nullptr;
+  if (cudaGraphAddNode(&cond, g, nullptr, nullptr, 0, &cp) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  if (cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(PPE_ERR_CUDA);
+  P->stream = bs;
+  ppe_status st = vc_iteration(P, h, 1);
+  P->stream = saved;
+  cudaGraph_t outb = nullptr;
+  if (cudaStreamEndCapture(bs, &outb) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+  if (st != PPE_OK) return fail(st);
+  if (cudaGraphInstantiate(&P->pcg_exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(bs);
+  P->prof_on = saved_prof;
+  return PPE_OK;
+}
+
 // Runs a refinement sequence.  Normally one graph launch (the loop runs on the
 // device); while per-kernel profiling is on, the same kernels are launched from
 // the host, which reads the test result after each check.
@@ -672,6 +786,9 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->line_len);
   cudaFree(P->fdf);
   cudaFree(P->rhs_part);
+  for (int i = 0; i < 8; ++i) cudaFree(P->vc[i]);
+  cudaFree(P->pcg_part);
+  if (P->pcg_exec) cudaGraphExecDestroy(P->pcg_exec);
   cudaFree(P->pdf);
   cudaFree(P->upre);
   cudaFree(P->vpre);
@@ -718,6 +835,10 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   const size_t zlim = P->fp32 ? zpass_smem_limit<float>() : zpass_smem_limit<double>();
   if (xs > xlim || zs > zlim || ys > lim) return PPE_ERR_INVALID_ARG;
   PPE_TRY(cudaStreamSynchronize(P->stream));
+  if (P->pcg_exec) {  // rebuilt with the new shapes on the next unsplit call
+    cudaGraphExecDestroy(P->pcg_exec);
+    P->pcg_exec = nullptr;
+  }
   P->tj = t->rhs_lines;
   P->kc = t->rhs_planes;
   P->lpb = t->x_lines;
@@ -838,6 +959,61 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
                                                 F->u_out, F->v_out, F->w_out, P->stream));
   }
   return PPE_OK;
+}
+
+ppe_status ppe_project_unsplit(ppe_plan_t P, const ppe_fields* F, double tol, int max_iter) {
+  if (!P || !F || !F->u || !F->v || !F->w || !F->S || !F->rho || !F->p || !F->u_out || !F->v_out || !F->w_out ||
+      !(F->dt > 0) || !(tol >= 0) || max_iter < 0 || max_iter > 100000)
+    return PPE_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  PPE_TRY(cudaStreamIsCapturing(P->stream, &cst));
+  if (cst != cudaStreamCaptureStatusNone) return PPE_ERR_INVALID_ARG;  // not capturable
+  ppe_status s = ensure_vc(P);
+  if (s != PPE_OK) return s;
+  if (!P->pcg_exec && (s = build_pcg_graph(P)) != PPE_OK) return s;
+  const VcConst C = make_vc_const(P->g, F->dt);
+  df** V = P->vc;
+  const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
+  PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, 1.0, P->opt.refine_tol, 0, P->stream));
+  PPE_TRY(cudaMemsetAsync(V[VC_X], 0, sizeof(df) * n, P->stream));
+  PPE_TRY(cudaMemsetAsync(V[VC_P], 0, sizeof(df) * n, P->stream));  // p0 = 0 p - zs needs finite p
+  PPE_LAUNCH(P, K_VC_SETUP, launch_vc_setup(P->gd, P->opt.face_rule, F->u, F->v, F->w, F->S, F->rho, C, V[VC_AX],
+                                            V[VC_AY], V[VC_AZ], V[VC_R], P->sc, P->pcg_part, P->stream));
+  PPE_LAUNCH(P, K_VC_SCALAR, launch_vc_start(P->gd, P->sc, P->pcg_part, tol, max_iter, P->stream));
+  // z0 = M^{-1} r0, rz0, p0 = z0
+  if ((s = vc_precond(P)) != PPE_OK) return s;
+  PPE_LAUNCH(P, K_VC_DOTS, launch_vc_dots(P->gd, V[VC_R], V[VC_ZS], V[VC_R], P->pcg_part, P->stream));
+  cudaGraphConditionalHandle none = 0;
+  PPE_LAUNCH(P, K_VC_SCALAR, launch_vc_beta(P->gd, P->sc, P->pcg_part, 1, none, 0, P->stream));
+  PPE_LAUNCH(P, K_VC_PUPDATE, launch_vc_pupdate(P->gd, V[VC_P], V[VC_ZS], P->sc, P->stream));
+  if (max_iter > 0) {
+    if (!P->prof_on) {
+      PPE_TRY(cudaGraphLaunch(P->pcg_exec, P->stream));
+    } else {
+      // per-kernel timing: the same iteration driven from the host
+      for (;;) {
+        int cont = 0;
+        PPE_TRY(cudaMemcpyAsync(&cont, &P->sc->pcg_cont, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+        PPE_TRY(cudaStreamSynchronize(P->stream));
+        if (!cont) break;
+        if ((s = vc_iteration(P, none, 0)) != PPE_OK) return s;
+      }
+    }
+  }
+  PPE_LAUNCH(P, K_VC_CORRECT, launch_vc_correct(P->gd, F->u, F->v, F->w, V[VC_X], V[VC_AX], V[VC_AY], V[VC_AZ], C,
+                                                P->sc, P->pcg_part, F->p, F->u_out, F->v_out, F->w_out,
+                                                P->stream));
+  return PPE_OK;
+}
+
+ppe_status ppe_unsplit_info(ppe_plan_t P, int* iterations, double* rel_residual) {
+  if (!P || !iterations || !rel_residual) return PPE_ERR_INVALID_ARG;
+  DevScalars h;
+  PPE_TRY(cudaMemcpyAsync(&h, P->sc, sizeof(h), cudaMemcpyDeviceToHost, P->stream));
+  PPE_TRY(cudaStreamSynchronize(P->stream));
+  *iterations = h.pcg_iter;
+  *rel_residual = h.pcg_rel;
+  return (h.pcg_rel <= h.pcg_tol) ? PPE_OK : PPE_ERR_NOT_CONVERGED;
 }
 
 struct ppe_batch_s {

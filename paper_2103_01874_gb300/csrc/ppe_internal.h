@@ -54,6 +54,15 @@ struct DevScalars {
   int f_ran;                                    // f_sum, f_mean belong to the current call
   int rhs_tiles, rhs_chunks;                    // tiling of the last k_rhs_march (0: none this call)
   int x_parts;                                  // CTAs of the last forward x transform of f (0: none)
+  // unsplit projection (k_pcg.cu): conjugate-gradient state
+  double pcg_alpha, pcg_beta, pcg_rz;           // step, direction update, r . z
+  double pcg_gmean;                             // mean of the right side g (kept by r)
+  df pcg_gmean_df;
+  df pcg_xmean_df;                              // mean of the solution, removed from p
+  double pcg_rel;                               // max |r - mean g| / max |g| after the last update
+  double pcg_tol;
+  unsigned long long pcg_gmax_bits, pcg_rmax_bits;
+  int pcg_iter, pcg_max, pcg_cont;
   double2* part;                                // per-CTA partial sums, plan workspace (2 ny nz entries):
                                                 //   [0, ny nz): k_rhs_march (wall flux, wall tiles only)
                                                 //   [ny nz, 2 ny nz): forward x transform (sum of f)
@@ -95,6 +104,35 @@ int rhs_max_lines(int nx);  // largest rhs_lines value (lines per thread stack, 
 cudaError_t set_rhs_smem_limit();
 size_t rhs_smem_limit();  // largest dynamic shared memory every k_rhs_march instance accepts
 constexpr size_t kSmemPerCta = 227 * 1024;  // opt-in shared memory per CTA (static + dynamic)
+
+// ---- unsplit projection (k_pcg.cu) ----
+// Constants of the variable-coefficient operator as pairs: 1/h^2, 1/h, 1/dt, dt h.
+struct VcConst {
+  df ix2, iy2, iz2;
+  df idx, idy, idz, idt;
+  df dthx, dthy, dthz;
+};
+unsigned vc_grid(size_t n);  // CTAs of the flat kernels (and their partial sums)
+cudaError_t launch_vc_setup(const GridDev& g, int rule, const double* u, const double* v, const double* w,
+                            const double* S, const double* rho, const VcConst& C, df* ax, df* ay, df* az, df* r,
+                            DevScalars* sc, double2* part, cudaStream_t st);
+cudaError_t launch_vc_start(const GridDev& g, DevScalars* sc, const double2* part, double tol, int max_iter,
+                            cudaStream_t st);
+cudaError_t launch_vc_apply(const GridDev& g, const df* p, const df* ax, const df* ay, const df* az, df* Kp,
+                            double2* part, cudaStream_t st);
+cudaError_t launch_vc_alpha(const GridDev& g, DevScalars* sc, const double2* part, cudaStream_t st);
+cudaError_t launch_vc_update(const GridDev& g, df* x, df* r, const df* p, const df* Kp, DevScalars* sc,
+                             cudaStream_t st);
+cudaError_t launch_vc_dots(const GridDev& g, const df* r, const df* zs, const df* Kp, double2* part,
+                           cudaStream_t st);
+cudaError_t launch_vc_beta(const GridDev& g, DevScalars* sc, const double2* part, int first,
+                           cudaGraphConditionalHandle handle, int use_handle, cudaStream_t st);
+cudaError_t launch_vc_pupdate(const GridDev& g, df* p, const df* zs, const DevScalars* sc, cudaStream_t st);
+// Eq. (29) and p with the mean of x removed (sum x, mean, correction)
+cudaError_t launch_vc_correct(const GridDev& g, const double* u, const double* v, const double* w, const df* x,
+                              const df* ax, const df* ay, const df* az, const VcConst& C, DevScalars* sc,
+                              double2* part, double* p_out, double* u_out, double* v_out, double* w_out,
+                              cudaStream_t st);
 
 // ---- launchers (k_spectral.cu) ----
 template <typename T>

@@ -91,6 +91,8 @@ SIGNATURES = {
     "ppe_project_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(FieldsC), c_void_p]),
     "ppe_set_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
+    "ppe_project_unsplit": (c_int, [c_void_p, POINTER(FieldsC), c_double, c_int]),
+    "ppe_unsplit_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
 }
 
 
@@ -292,6 +294,21 @@ class Plan:
     def project_host(self, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
         fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
         _check(lib().ppe_project_host(self._h, ctypes.byref(fc)), "ppe_project_host")
+
+    def project_unsplit(self, u, v, w, S, rho, dt, p, u_out, v_out, w_out, tol=1e-10, max_iter=500):
+        """The unsplit projection, Eqs. (29)-(30), by FFT-preconditioned CG (ppe_project_unsplit)."""
+        fc = self._fields(_ptr, u, v, w, S, rho, None, None, dt, p, u_out, v_out, w_out)
+        _check(lib().ppe_project_unsplit(self._h, ctypes.byref(fc), float(tol), int(max_iter)),
+               "ppe_project_unsplit")
+
+    def unsplit_info(self, allow_not_converged=False):
+        """(iterations, relative residual) of the last unsplit projection."""
+        it = c_int()
+        rel = c_double()
+        code = lib().ppe_unsplit_info(self._h, ctypes.byref(it), ctypes.byref(rel))
+        if not (code == 5 and allow_not_converged):
+            _check(code, "ppe_unsplit_info")
+        return it.value, rel.value
 
     def info(self, allow_not_converged=False, allow_incompatible=False) -> Info:
         inf = Info()
