@@ -367,6 +367,8 @@ def run_gpu(args):
         "gpu_launches_note": "kernels per timed region of the headline form (profiled re-run of the same steps)",
         "profiled_ms_per_step": ms32p / steps,
     }
+    if args.unsplit:
+        res["unsplit"] = run_unsplit(plan32, d, out, fl, per_step32, stream)
     if args.batched:
         res["batched"] = run_batched(args, dev)
     if args.served:
@@ -376,6 +378,33 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return res
+
+
+# ---------------------------------------------------------------------------
+# the unsplit projection (Eqs. (29)-(30)) on the same fields: the baseline the
+# split method replaces
+# ---------------------------------------------------------------------------
+def run_unsplit(plan, d, out, fl, split_ms, stream, reps=3, tol=1e-10):
+    import torch
+
+    def once():
+        plan.project_unsplit(d["u"], d["v"], d["w"], d["S"], d["rho"], fl.dt, out["p"], out["u"], out["v"], out["w"],
+                             tol=tol, max_iter=1000)
+    once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    it, rel = plan.unsplit_info(allow_not_converged=True)
+    return {"what": "variable-coefficient Eq. (30) by conjugate gradients preconditioned with the FP32 FFT solve "
+                    f"(Polak-Ribiere), from p = 0 to max|r| <= {tol:g} max|g|, then Eq. (29); same fields",
+            "ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iterations": it, "rel_residual": rel,
+            "ms_per_iteration": ms / max(it, 1), "split_speedup": ms / split_ms}
 
 
 # ---------------------------------------------------------------------------
@@ -558,6 +587,7 @@ def main():
     ap.add_argument("--no-kernel-times", dest="kernel_times", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-served", dest="served", action="store_false")
+    ap.add_argument("--no-unsplit", dest="unsplit", action="store_false")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--host-refine", action="store_true",
                     help="drive every timed step with per-kernel events (refinement loop from the host), so that a "
