@@ -369,6 +369,7 @@ def run_gpu(args):
     }
     if args.unsplit:
         res["unsplit"] = run_unsplit(plan32, d, out, fl, per_step32, stream)
+        res["divergence_constraint"] = run_div_constraint(plan32, dev, stream, hbm)
     if args.batched:
         res["batched"] = run_batched(args, dev)
     if args.served:
@@ -405,6 +406,36 @@ def run_unsplit(plan, d, out, fl, split_ms, stream, reps=3, tol=1e-10):
                     f"(Polak-Ribiere), from p = 0 to max|r| <= {tol:g} max|g|, then Eq. (29); same fields",
             "ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iterations": it, "rel_residual": rel,
             "ms_per_iteration": ms / max(it, 1), "split_speedup": ms / split_ms}
+
+
+def run_div_constraint(plan, dev, stream, hbm, reps=20):
+    """Eq. (31) at the bench grid: 6 FP64 inputs and a byte mask in, S and the
+    one-fluid density out (65 B per cell)."""
+    import torch
+    n = (NZ, NY, NX)
+    g = torch.Generator(device=dev).manual_seed(7)
+    C = torch.rand(n, generator=g, device=dev, dtype=torch.float64)
+    ins = [C] + [torch.randn(n, generator=g, device=dev, dtype=torch.float64) for _ in range(3)]
+    ins += [50.0 + 80.0 * torch.rand(n, generator=g, device=dev, dtype=torch.float64),
+            600.0 + 100.0 * torch.rand(n, generator=g, device=dev, dtype=torch.float64)]
+    mask = (torch.rand(n, generator=g, device=dev) < 0.1).to(torch.uint8)
+    S = torch.empty_like(C)
+    rho = torch.empty_like(C)
+    plan.divergence_constraint(*ins, S, rho=rho, under_resolved=mask)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.divergence_constraint(*ins, S, rho=rho, under_resolved=mask)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    nbytes = N_CELLS * (6 * 8 + 1 + 2 * 8)
+    del ins, S, rho, mask
+    return {"what": "Eq. (31): S and the one-fluid density from C, phase compressibilities, mdot, phase densities "
+                    "and an under-resolved mask", "us_per_launch": us, "GBps": nbytes / (us * 1e-6) / 1e9,
+            "frac_of_hbm": nbytes / (us * 1e-6) / 1e9 / hbm, "bytes_per_launch": nbytes}
 
 
 # ---------------------------------------------------------------------------

@@ -172,6 +172,22 @@ ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
  * ppe_get_info does. */
 ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
 
+/* Eq. (31): the divergence constraint S = div u^{n+1} from the phase-wise
+ * quantities (all device arrays of nx*ny*nz cells, cell layout):
+ *   S = -(1 - C) comp_g - C comp_l + mdot (1/rho_g - 1/rho_l)
+ * with C the liquid volume fraction in [0, 1], comp_f = (1/rho_f) D rho_f/Dt
+ * the phase compressibilities, mdot the volumetric phase-change rate (> 0 for
+ * liquid turning into gas) and rho_g, rho_l > 0 the phase densities.  Where
+ * under_resolved[c] != 0 and 0 < C < 1 (an under-resolved interface cell) S is
+ * 0, the paper's treatment of under-resolved regions; under_resolved may be
+ * NULL.  When rho is non-NULL it receives the one-fluid density
+ * rho_g (1 - C) + rho_l C.  Evaluated in float pairs (relative ~1e-15), on the
+ * plan's stream.  The result is an input of ppe_project (S) and, for the
+ * density, of ppe_project and ppe_project_unsplit (rho). */
+ppe_status ppe_divergence_constraint(ppe_plan_t plan, const double* C, const double* comp_g, const double* comp_l,
+                                     const double* mdot, const double* rho_g, const double* rho_l,
+                                     const unsigned char* under_resolved, double* S, double* rho);
+
 /* The unsplit projection, Eqs. (29)-(30) -- the iterative baseline that the
  * split method replaces.  The variable-coefficient equation
  *   D[(1/rho_f) G p] = (D u* - S) / dt

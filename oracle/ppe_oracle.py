@@ -285,6 +285,26 @@ def unsplit_residual(p, g, rho, lengths, rule=FACE_ARITHMETIC):
     return float(np.max(np.abs(r)) / np.max(np.abs(gc)))
 
 
+# ----------------------------------------------------------------------------
+# Eq. (31): the divergence constraint S from the phase-wise quantities
+# ----------------------------------------------------------------------------
+
+def divergence_constraint(C, comp_g, comp_l, mdot, rho_g, rho_l, under_resolved=None):
+    """S = div u^{n+1} = -(1 - C) comp_g - C comp_l + mdot (1/rho_g - 1/rho_l),
+    Eq. (31), with comp_f = (1/rho_f) D rho_f / Dt the phase compressibilities
+    and mdot the volumetric phase-change rate (> 0 for liquid turning into gas).
+    In under-resolved interface cells (mask set and 0 < C < 1) the one-fluid
+    divergence is set to zero (the treatment of under-resolved regions in the
+    extrapolation section of the paper).  Also returns the one-fluid density
+    rho = rho_g (1 - C) + rho_l C of the volume-fraction substitution that
+    precedes Eq. (31)."""
+    S = -(1.0 - C) * comp_g - C * comp_l + mdot * (1.0 / rho_g - 1.0 / rho_l)
+    if under_resolved is not None:
+        S = np.where((under_resolved != 0) & (C > 0.0) & (C < 1.0), 0.0, S)
+    rho = rho_g * (1.0 - C) + rho_l * C
+    return S, rho
+
+
 def rel_linf(a, b):
     """max|a - b| / max|b|."""
     a = np.asarray(a)

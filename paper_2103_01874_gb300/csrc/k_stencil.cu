@@ -275,6 +275,33 @@ __global__ void k_set_rho0(DevScalars* sc, double rho0) {
   if (threadIdx.x == 0) sc->rho0_bits = (unsigned long long)__double_as_longlong(rho0);
 }
 
+// Eq. (31): S = -(1 - C) comp_g - C comp_l + mdot (1/rho_g - 1/rho_l) in pairs;
+// zero in under-resolved interface cells (mask set, 0 < C < 1); the one-fluid
+// density rho = rho_g (1 - C) + rho_l C when rho is given.  C's range tests
+// run on the FP64 bit pattern (C >= 0).
+__global__ void __launch_bounds__(256) k_div_constraint(size_t n, const double* __restrict__ C,
+                                                        const double* __restrict__ comp_g,
+                                                        const double* __restrict__ comp_l,
+                                                        const double* __restrict__ mdot,
+                                                        const double* __restrict__ rho_g,
+                                                        const double* __restrict__ rho_l,
+                                                        const unsigned char* __restrict__ mask, double* S,
+                                                        double* rho) {
+  const df one = {1.0f, 0.0f};
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const double cd = __ldg(C + c);
+    const df vc = d2df(cd);
+    const df rg = d2df(__ldg(rho_g + c)), rl = d2df(__ldg(rho_l + c));
+    const df omc = df_subz(one, vc);  // 1 - C
+    const df s = df_addz(df_subz(df_neg(df_mulz(omc, d2df(__ldg(comp_g + c)))), df_mulz(vc, d2df(__ldg(comp_l + c)))),
+                         df_mulz(d2df(__ldg(mdot + c)), df_subz(df_recip(rg), df_recip(rl))));
+    const unsigned long long cb = (unsigned long long)__double_as_longlong(cd);
+    const bool interface_cell = cb > 0ull && cb < 0x3FF0000000000000ull;  // 0 < C < 1
+    S[c] = (mask && mask[c] && interface_cell) ? 0.0 : df2d(s);
+    if (rho) rho[c] = df2d(df_addz(df_mulz(rg, omc), df_mulz(rl, vc)));
+  }
+}
+
 namespace {
 unsigned grid_for(size_t total, size_t cap) {
   size_t b = (total + 255) / 256;
@@ -283,6 +310,14 @@ unsigned grid_for(size_t total, size_t cap) {
   return (unsigned)b;
 }
 }  // namespace
+
+cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_g, const double* comp_l,
+                                  const double* mdot, const double* rho_g, const double* rho_l,
+                                  const unsigned char* mask, double* S, double* rho, cudaStream_t st) {
+  k_div_constraint<<<grid_for(n, (size_t)152 * 16), 256, 0, st>>>(n, C, comp_g, comp_l, mdot, rho_g, rho_l, mask, S,
+                                                                  rho);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st) {
   k_init_scalars<<<1, 32, 0, st>>>(sc, rho0, tol, keep_rho0);

@@ -257,12 +257,13 @@ ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_E
 // Kernel names reported by ppe_profile_read.
 enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
                 K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_VC_SETUP, K_VC_APPLY, K_VC_UPDATE,
-                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_COUNT };
+                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_DIV_S, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
                                            "k_xfwd_resid", "k_zfft_fwd", "k_ysolve", "k_zfft_inv",
                                            "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
                                            "k_df_to_d", "k_vc_setup", "k_vc_apply", "k_vc_update",
-                                           "k_vc_dots", "k_vc_pupdate", "k_vc_scalars", "k_vc_correct"};
+                                           "k_vc_dots", "k_vc_pupdate", "k_vc_scalars", "k_vc_correct",
+                                           "k_div_constraint"};
 constexpr int kProfMax = 16384;
 
 int prof_begin(ppe_plan_t P, int id) {
@@ -1003,6 +1004,16 @@ ppe_status ppe_project_unsplit(ppe_plan_t P, const ppe_fields* F, double tol, in
   PPE_LAUNCH(P, K_VC_CORRECT, launch_vc_correct(P->gd, F->u, F->v, F->w, V[VC_X], V[VC_AX], V[VC_AY], V[VC_AZ], C,
                                                 P->sc, P->pcg_part, F->p, F->u_out, F->v_out, F->w_out,
                                                 P->stream));
+  return PPE_OK;
+}
+
+ppe_status ppe_divergence_constraint(ppe_plan_t P, const double* C, const double* comp_g, const double* comp_l,
+                                     const double* mdot, const double* rho_g, const double* rho_l,
+                                     const unsigned char* under_resolved, double* S, double* rho) {
+  if (!P || !C || !comp_g || !comp_l || !mdot || !rho_g || !rho_l || !S) return PPE_ERR_INVALID_ARG;
+  const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
+  PPE_LAUNCH(P, K_DIV_S, launch_div_constraint(n, C, comp_g, comp_l, mdot, rho_g, rho_l, under_resolved, S, rho,
+                                               P->stream));
   return PPE_OK;
 }
 

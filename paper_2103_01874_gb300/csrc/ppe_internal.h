@@ -168,6 +168,10 @@ template <typename T>
 size_t zpass_smem_limit();  // the same for the z pass
 
 // ---- launchers (k_stencil.cu) ----
+// Eq. (31) divergence constraint (and the one-fluid density when rho != NULL)
+cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_g, const double* comp_l,
+                                  const double* mdot, const double* rho_g, const double* rho_l,
+                                  const unsigned char* mask, double* S, double* rho, cudaStream_t st);
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st);
 cudaError_t launch_set_rho0(DevScalars* sc, double rho0, cudaStream_t st);
 // Forms sc->K from sc->rho0, dt and the grid (one thread).

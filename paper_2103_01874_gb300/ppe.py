@@ -93,6 +93,7 @@ SIGNATURES = {
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
     "ppe_project_unsplit": (c_int, [c_void_p, POINTER(FieldsC), c_double, c_int]),
     "ppe_unsplit_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
+    "ppe_divergence_constraint": (c_int, [c_void_p] + [c_void_p] * 9),
 }
 
 
@@ -300,6 +301,21 @@ class Plan:
         fc = self._fields(_ptr, u, v, w, S, rho, None, None, dt, p, u_out, v_out, w_out)
         _check(lib().ppe_project_unsplit(self._h, ctypes.byref(fc), float(tol), int(max_iter)),
                "ppe_project_unsplit")
+
+    def divergence_constraint(self, C, comp_g, comp_l, mdot, rho_g, rho_l, S, rho=None, under_resolved=None):
+        """Eq. (31) into S (and the one-fluid density into rho); under_resolved a uint8 mask or None."""
+        c = self.cell_shape
+        mask = None
+        if under_resolved is not None:
+            import torch
+            if under_resolved.dtype != torch.uint8 or not under_resolved.is_cuda or \
+                    tuple(under_resolved.shape) != tuple(c) or not under_resolved.is_contiguous():
+                raise ValueError("under_resolved: need a contiguous uint8 CUDA tensor of the cell shape")
+            mask = under_resolved.data_ptr()
+        _check(lib().ppe_divergence_constraint(self._h, _ptr(C, c, "C"), _ptr(comp_g, c, "comp_g"),
+                                               _ptr(comp_l, c, "comp_l"), _ptr(mdot, c, "mdot"),
+                                               _ptr(rho_g, c, "rho_g"), _ptr(rho_l, c, "rho_l"), mask,
+                                               _ptr(S, c, "S"), _ptr(rho, c, "rho")), "ppe_divergence_constraint")
 
     def unsplit_info(self, allow_not_converged=False):
         """(iterations, relative residual) of the last unsplit projection."""

@@ -375,3 +375,54 @@ def test_planted_unsplit_density_mistake_is_caught():
     r0 = O.rho0_of(fl.rho)
     bad = O.div(fl.u - fl.dt * gx / r0, fl.v - fl.dt * gy / r0, fl.w - fl.dt * gz / r0, h)
     assert np.max(np.abs(bad - fl.S)) > 1e-3 * np.max(np.abs(fl.S))
+
+
+def _eq31_inputs(shape=(6, 5, 4), seed=3):
+    rng = np.random.default_rng(seed)
+    C = rng.choice([0.0, 1.0, 0.3, 0.7], size=shape)
+    comp_g = rng.normal(0.0, 2.0, shape)
+    comp_l = rng.normal(0.0, 0.1, shape)
+    mdot = np.where((C > 0) & (C < 1), rng.uniform(-1.0, 3.0, shape), 0.0)
+    rho_g = rng.uniform(50.0, 130.0, shape)
+    rho_l = rng.uniform(600.0, 700.0, shape)
+    mask = (rng.random(shape) < 0.3).astype(np.uint8)
+    return C, comp_g, comp_l, mdot, rho_g, rho_l, mask
+
+
+def test_divergence_constraint_limits_and_loop():
+    """Eq. (31): pure phases reduce to -(1/rho) D rho/Dt of that phase; no
+    compressibility and equal densities give S = 0; evaporation (mdot > 0,
+    rho_l > rho_g) expands (S > 0); the masked interface cells are zero and
+    only those; a scalar loop agrees with the vectorised form."""
+    C, cg, cl, md, rg, rl, mask = _eq31_inputs()
+    S, rho = O.divergence_constraint(C, cg, cl, md, rg, rl, mask)
+    gas, liq, itf = C == 0.0, C == 1.0, (C > 0) & (C < 1)
+    assert np.array_equal(S[gas], -cg[gas]) and np.array_equal(S[liq], -cl[liq])
+    assert np.all(S[itf & (mask != 0)] == 0.0)
+    assert np.array_equal(rho[gas], rg[gas]) and np.array_equal(rho[liq], rl[liq])
+    z = np.zeros_like(C)
+    S0, _ = O.divergence_constraint(C, z, z, md, rg, rg)
+    assert np.all(S0 == 0.0)
+    Se, _ = O.divergence_constraint(np.full_like(C, 0.5), z, z, np.ones_like(C), rg, rl)
+    assert np.all(Se > 0.0)
+    for idx in np.ndindex(C.shape):
+        c = C[idx]
+        s = -(1 - c) * cg[idx] - c * cl[idx] + md[idx] * (1 / rg[idx] - 1 / rl[idx])
+        if mask[idx] and 0 < c < 1:
+            s = 0.0
+        assert abs(s - S[idx]) <= 1e-15 * max(1.0, abs(s))
+        assert abs(rg[idx] + (rl[idx] - rg[idx]) * c - rho[idx]) <= 1e-13 * rho[idx]
+
+
+def test_planted_phase_change_sign_is_caught(monkeypatch):
+    """Swapping 1/rho_g and 1/rho_l in the phase-change term must fail the
+    expansion check."""
+    good = O.divergence_constraint
+
+    def bad(C, cg, cl, md, rg, rl, mask=None):
+        return good(C, cg, cl, md, rl, rg, mask)
+    monkeypatch.setattr(O, "divergence_constraint", bad)
+    C, cg, cl, md, rg, rl, mask = _eq31_inputs()
+    z = np.zeros_like(C)
+    Se, _ = O.divergence_constraint(np.full_like(C, 0.5), z, z, np.ones_like(C), rg, rl)
+    assert not np.all(Se > 0.0)
