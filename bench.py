@@ -370,6 +370,12 @@ def run_gpu(args):
     if args.unsplit:
         res["unsplit"] = run_unsplit(plan32, d, out, fl, per_step32, stream)
         res["divergence_constraint"] = run_div_constraint(plan32, dev, stream, hbm)
+        from paper_2103_01874_gb300 import split_study
+        res["split_study"] = {
+            "what": "max over 40 steps of max|p_split - p_exact| / max|p_exact| when the unsplit pressure is "
+                    "P(t) = Q cos(omega t) + R sin(omega t) (phi = omega dt per step); exact_history: p^n, p^{n-1} "
+                    "exact; 64^3 multimode, FP64 plan",
+            "rows": split_study.sweep(n=64)}
     if args.batched:
         res["batched"] = run_batched(args, dev)
     if args.served:

@@ -155,3 +155,23 @@ def batch_shapes(count: int = 64, seed: int = 3):
     rng = np.random.default_rng(seed)
     dims = np.asarray(BATCH_DIMS)
     return [tuple(int(d) for d in rng.choice(dims, size=3)) for _ in range(count)]
+
+
+def smooth_field(nx: int, ny: int, nz: int, *, seed: int = 0, modes: int = 4, amplitude: float = 1.0,
+                 lx: float = TWO_PI, lz: float = TWO_PI) -> np.ndarray:
+    """A smooth zero-mean cell field: `modes` products of a Fourier mode in x and
+    z (wavenumbers 1..3) and a cosine mode in y (1..3) with random phases and
+    N(0, 1) weights, scaled to max |.| = amplitude.  A stand-in for a pressure
+    field that varies slowly in space (the time signal of the split study)."""
+    rng = np.random.default_rng(seed)
+    x = _centres(nx, lx)[None, None, :]
+    zc = _centres(nz, lz)[:, None, None]
+    jj = (np.arange(ny, dtype=np.float64) + 0.5)[None, :, None]
+    out = np.zeros((nz, ny, nx))
+    for _ in range(modes):
+        a, b, c = rng.integers(1, 4, size=3)
+        px, pz = rng.uniform(0.0, TWO_PI, size=2)
+        out += rng.standard_normal() * (np.cos(TWO_PI * a * x / lx + px) * np.cos(math.pi * b * jj / ny)
+                                        * np.cos(TWO_PI * c * zc / lz + pz))
+    out -= out.mean()
+    return amplitude * out / np.abs(out).max()
