@@ -514,6 +514,7 @@ def run_served(args, dev):
     ex = serve.CudaExecutor(slots=8, device=dev.index)
     for s in set(r.shape for r in reqs):
         ex.template(s)  # resident input templates, generated before the clock starts
+    ex.prealloc(shapes)  # per-slot field buffers
     srv = serve.Server(ex, budget_bytes=150 << 30, slots=8)
     # steady state: an untimed replay of an arrival trace of the same law (other
     # seed) lets the plan pool grow to what concurrent requests of each size class

@@ -181,7 +181,7 @@ ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
  * under_resolved[c] != 0 and 0 < C < 1 (an under-resolved interface cell) S is
  * 0, the paper's treatment of under-resolved regions; under_resolved may be
  * NULL.  When rho is non-NULL it receives the one-fluid density
- * rho_g (1 - C) + rho_l C.  Evaluated in float pairs (relative ~1e-15), on the
+ * rho_g (1 - C) + rho_l C.  Evaluated in float pairs (relative error < 5e-14), on the
  * plan's stream.  The result is an input of ppe_project (S) and, for the
  * density, of ppe_project and ppe_project_unsplit (rho). */
 ppe_status ppe_divergence_constraint(ppe_plan_t plan, const double* C, const double* comp_g, const double* comp_l,

@@ -194,9 +194,12 @@ class Server:
 
 
 class CudaExecutor:
-    """libppe on one GPU: slot streams, resident per-shape input templates
-    (each admitted request gets its own copies of the seven input fields and
-    four output fields), ppe_project on the slot's stream, completion events."""
+    """libppe on one GPU: slot streams, resident per-shape input templates,
+    ppe_project on the slot's stream, completion events.  Each slot keeps one
+    set of field buffers (seven inputs, four outputs) per shape it has served,
+    so that a request copies its inputs device to device instead of allocating
+    (an allocation can synchronise the whole device); `prealloc` creates them
+    up front."""
 
     def __init__(self, slots: int = 8, device=None, templates=None, autotune_cache=None):
         import torch
@@ -208,6 +211,25 @@ class CudaExecutor:
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
         self.templates = templates if templates is not None else {}
         self.autotune_cache = autotune_cache
+        self.buffers = {}  # (slot, shape) -> (inputs, outputs)
+
+    def _bufs(self, slot, shape):
+        b = self.buffers.get((slot, shape))
+        if b is None:
+            torch = self.torch
+            tmpl, _ = self.template(shape)
+            with torch.cuda.stream(self.streams[slot]):
+                d = {k: torch.empty_like(v) for k, v in tmpl.items()}
+                out = dict(p=torch.empty_like(d["rho"]), u=torch.empty_like(d["u"]), v=torch.empty_like(d["v"]),
+                           w=torch.empty_like(d["w"]))
+            b = self.buffers[(slot, shape)] = (d, out)
+        return b
+
+    def prealloc(self, shapes):
+        for slot in range(len(self.streams)):
+            for shape in shapes:
+                self._bufs(slot, shape)
+        self.torch.cuda.synchronize(self.dev)
 
     def template(self, shape):
         t = self.templates.get(shape)
@@ -249,10 +271,10 @@ class CudaExecutor:
         torch = self.torch
         s = self.streams[slot]
         tmpl, fl = self.template(req.shape)
+        d, out = self._bufs(slot, req.shape)
         with torch.cuda.stream(s):
-            d = {k: v.clone() for k, v in tmpl.items()}  # this request's resident fields
-            out = dict(p=torch.empty_like(d["rho"]), u=torch.empty_like(d["u"]), v=torch.empty_like(d["v"]),
-                       w=torch.empty_like(d["w"]))
+            for k, v in tmpl.items():  # this request's fields, in the slot's buffers
+                d[k].copy_(v, non_blocking=True)
         plan.set_stream(s)
         plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, out["p"], out["u"],
                      out["v"], out["w"])
@@ -271,7 +293,7 @@ class CudaExecutor:
         return {k: v.cpu().numpy() for k, v in h["out"].items()}
 
     def release(self, h):
-        h["d"] = h["out"] = None
+        h["d"] = h["out"] = None  # the slot's buffers are reused by its next request
 
 
 class FakeExecutor:

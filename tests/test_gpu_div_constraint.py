@@ -49,8 +49,9 @@ def test_matches_oracle(shape, use_mask):
     mask = mask if use_mask else None
     S_ref, rho_ref = O.divergence_constraint(C, cg, cl, md, rg, rl, mask)
     S, rho = _gpu(shape, (C, cg, cl, md, rg, rl), mask)
-    assert O.rel_linf(S, S_ref) <= 1e-14
-    assert O.rel_linf(rho, rho_ref) <= 1e-14
+    # a handful of lazy pair operations, each within ~2^-47 relative
+    assert O.rel_linf(S, S_ref) <= 5e-14
+    assert O.rel_linf(rho, rho_ref) <= 5e-14
     if use_mask:
         zero = (mask != 0) & (C > 0) & (C < 1)
         assert np.all(S[zero] == 0.0) and np.any(S[~zero] != 0.0)
@@ -62,7 +63,7 @@ def test_full_size_and_without_density():
     S_ref, _ = O.divergence_constraint(C, cg, cl, md, rg, rl, mask)
     S, rho = _gpu(shape, (C, cg, cl, md, rg, rl), mask, with_rho=False)
     assert rho is None
-    assert O.rel_linf(S, S_ref) <= 1e-14
+    assert O.rel_linf(S, S_ref) <= 5e-14
 
 
 def test_assembled_constraint_drives_the_projection():
