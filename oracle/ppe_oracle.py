@@ -43,6 +43,11 @@ import scipy.fft as sfft
 FACE_ARITHMETIC = 0
 FACE_HARMONIC = 1
 
+# top boundary in y (the bottom, y = 0, is always a wall)
+BC_WALL = 0      # no penetration, homogeneous Neumann for p
+BC_OUTFLOW = 1   # open boundary: p = 0 on the top face (the paper's outflow
+                 # condition of its jet cases, Sec. 6); v there is not fixed
+
 
 def spacings(shape, lengths):
     nz, ny, nx = shape
@@ -54,16 +59,20 @@ def spacings(shape, lengths):
 # Discrete operators on the staggered mesh (Sec. 5, uniform MAC grid)
 # ----------------------------------------------------------------------------
 
-def grad(q, h):
+def grad(q, h, bc_top=BC_WALL):
     """G: cell field [Nz][Ny][Nx] -> face fields (gx [Nz][Ny][Nx],
     gy [Nz][Ny+1][Nx], gz [Nz][Ny][Nx]).  gx[..., i] = (q_i - q_{i-1})/dx with
-    periodic wrap; gy on the walls j = 0, Ny is zero (homogeneous Neumann)."""
+    periodic wrap; gy on the walls j = 0, Ny is zero (homogeneous Neumann).
+    With an outflow top, q = 0 on the face j = Ny, half a cell above the last
+    centre: gy[Ny] = (0 - q_{Ny-1}) / (dy/2)."""
     dx, dy, dz = h
     nz, ny, nx = q.shape
     gx = (q - np.roll(q, 1, axis=2)) / dx
     gz = (q - np.roll(q, 1, axis=0)) / dz
     gy = np.zeros((nz, ny + 1, nx))
     gy[:, 1:ny, :] = (q[:, 1:, :] - q[:, :-1, :]) / dy
+    if bc_top == BC_OUTFLOW:
+        gy[:, ny, :] = -2.0 * q[:, ny - 1, :] / dy
     return gx, gy, gz
 
 
@@ -76,9 +85,9 @@ def div(a, b, c, h):
             + (np.roll(c, -1, axis=0) - c) / dz)
 
 
-def laplacian(q, h):
+def laplacian(q, h, bc_top=BC_WALL):
     """L = D G, the 7-point operator of Eq. (34)'s left side."""
-    return div(*grad(q, h), h)
+    return div(*grad(q, h, bc_top), h)
 
 
 def face_density(rho, rule=FACE_ARITHMETIC):
@@ -113,12 +122,12 @@ def rho0_of(rho):
 # Eq. (34): right-hand side
 # ----------------------------------------------------------------------------
 
-def ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC):
+def ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC, bc_top=BC_WALL):
     """f = D[(1 - rho_0/rho_f) G p_hat] + (rho_0/dt)(D u* - S), Eq. (34), with
     p_hat = 2 p^n - p^{n-1} (Eq. (32))."""
     h = spacings(rho.shape, lengths)
     p_hat = 2.0 * p_n - p_nm1
-    gx, gy, gz = grad(p_hat, h)
+    gx, gy, gz = grad(p_hat, h, bc_top)
     rx, ry, rz = face_density(rho, rule)
     split = div((1.0 - rho0 / rx) * gx, (1.0 - rho0 / ry) * gy, (1.0 - rho0 / rz) * gz, h)
     return split + (rho0 / dt) * (div(u, v, w, h) - S)
@@ -143,13 +152,15 @@ def compatibility(v, S, lengths):
                 wall_vmax=float(np.abs(wall).max()))
 
 
-def eigenvalues(shape, lengths):
+def eigenvalues(shape, lengths, bc_top=BC_WALL):
     """Eigenvalues of L for the Fourier (x, z) x cosine (y) modes, shape
-    [Nz][Ny][Nx//2+1] matching rfft in x, full fft in z, DCT-II in y."""
+    [Nz][Ny][Nx//2+1] matching rfft in x, full fft in z, and in y DCT-II
+    (walls: cos(pi k (j + 1/2)/Ny)) or DCT-IV (outflow top:
+    cos(pi (k + 1/2)(j + 1/2)/Ny), which vanish on the top face)."""
     nz, ny, nx = shape
     dx, dy, dz = spacings(shape, lengths)
     kx = np.arange(nx // 2 + 1)
-    ky = np.arange(ny)
+    ky = np.arange(ny) + (0.5 if bc_top == BC_OUTFLOW else 0.0)
     kz = np.arange(nz)
     lx = -(4.0 / dx**2) * np.sin(math.pi * kx / nx) ** 2
     ly = -(4.0 / dy**2) * np.sin(math.pi * ky / (2 * ny)) ** 2
@@ -157,11 +168,18 @@ def eigenvalues(shape, lengths):
     return lz[:, None, None] + ly[None, :, None] + lx[None, None, :]
 
 
-def ppe_solve(f, lengths):
-    """Zero-mean p with L p = f - mean(f) (the zero mode is dropped)."""
+def ppe_solve(f, lengths, bc_top=BC_WALL):
+    """Walls: zero-mean p with L p = f - mean(f) (the zero mode is dropped).
+    Outflow top: the unique p with L p = f (no zero mode)."""
     nz, ny, nx = f.shape
     fh = np.fft.rfft(f, axis=2)
     fh = np.fft.fft(fh, axis=0)
+    if bc_top == BC_OUTFLOW:
+        fh = sfft.dct(fh, type=4, axis=1, norm="ortho")
+        ph = fh / eigenvalues(f.shape, lengths, bc_top)
+        ph = sfft.idct(ph, type=4, axis=1, norm="ortho")
+        ph = np.fft.ifft(ph, axis=0)
+        return np.fft.irfft(ph, n=nx, axis=2)
     fh = sfft.dct(fh, type=2, axis=1, norm="ortho")
     lam = eigenvalues(f.shape, lengths)
     lam[0, 0, 0] = 1.0
@@ -172,22 +190,23 @@ def ppe_solve(f, lengths):
     return np.fft.irfft(ph, n=nx, axis=2)
 
 
-def residual(f, p, lengths):
+def residual(f, p, lengths, bc_top=BC_WALL):
     h = spacings(f.shape, lengths)
-    return f - laplacian(p, h)
+    return f - laplacian(p, h, bc_top)
 
 
 # ----------------------------------------------------------------------------
 # Eq. (33): velocity correction
 # ----------------------------------------------------------------------------
 
-def ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC):
+def ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHMETIC, bc_top=BC_WALL):
     """u^{n+1} = u* - dt [G p / rho_0 + (1/rho_f - 1/rho_0) G p_hat] on every
-    face, Eq. (33).  On the wall faces G = 0, so v is returned unchanged."""
+    face, Eq. (33).  On the wall faces G = 0, so v is returned unchanged there;
+    an outflow top face is corrected like an interior face."""
     h = spacings(rho.shape, lengths)
     p_hat = 2.0 * p_n - p_nm1
-    gpx, gpy, gpz = grad(p, h)
-    ghx, ghy, ghz = grad(p_hat, h)
+    gpx, gpy, gpz = grad(p, h, bc_top)
+    ghx, ghy, ghz = grad(p_hat, h, bc_top)
     rx, ry, rz = face_density(rho, rule)
     u1 = u - dt * (gpx / rho0 + (1.0 / rx - 1.0 / rho0) * ghx)
     v1 = v - dt * (gpy / rho0 + (1.0 / ry - 1.0 / rho0) * ghy)
@@ -195,30 +214,30 @@ def ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule=FACE_ARITHM
     return u1, v1, w1
 
 
-def ppe_project(u, v, w, S, rho, p_n, p_nm1, dt, lengths, rho0=None, rule=FACE_ARITHMETIC):
+def ppe_project(u, v, w, S, rho, p_n, p_nm1, dt, lengths, rho0=None, rule=FACE_ARITHMETIC, bc_top=BC_WALL):
     """The whole projection step: returns dict(f, p, u, v, w, rho0)."""
     if rho0 is None or rho0 <= 0.0:
         rho0 = rho0_of(rho)
-    f = ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule)
-    p = ppe_solve(f, lengths)
-    u1, v1, w1 = ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule)
+    f = ppe_rhs(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule, bc_top)
+    p = ppe_solve(f, lengths, bc_top)
+    u1, v1, w1 = ppe_correct(u, v, w, rho, p, p_n, p_nm1, rho0, dt, lengths, rule, bc_top)
     return dict(f=f, p=p, u=u1, v=v1, w=w1, rho0=rho0)
 
 
-def project_fields(fl, rule=FACE_ARITHMETIC, rho0=None):
+def project_fields(fl, rule=FACE_ARITHMETIC, rho0=None, bc_top=BC_WALL):
     """ppe_project on a paper_2103_01874_gb300.fields.Fields-like object."""
     return ppe_project(fl.u, fl.v, fl.w, fl.S, fl.rho, fl.p_n, fl.p_nm1, fl.dt,
-                       (fl.lx, fl.ly, fl.lz), rho0=rho0, rule=rule)
+                       (fl.lx, fl.ly, fl.lz), rho0=rho0, rule=rule, bc_top=bc_top)
 
 
 # ----------------------------------------------------------------------------
 # Eq. (30): the unsplit variable-coefficient equation (exactness reference)
 # ----------------------------------------------------------------------------
 
-def var_coeff_apply(q, rho, lengths, rule=FACE_ARITHMETIC):
+def var_coeff_apply(q, rho, lengths, rule=FACE_ARITHMETIC, bc_top=BC_WALL):
     """A q = D[(1/rho_f) G q], the left side of Eq. (30)."""
     h = spacings(rho.shape, lengths)
-    gx, gy, gz = grad(q, h)
+    gx, gy, gz = grad(q, h, bc_top)
     rx, ry, rz = face_density(rho, rule)
     return div(gx / rx, gy / ry, gz / rz, h)
 
@@ -248,9 +267,12 @@ def dense_zero_mean_solve(mat, rhs):
     return np.linalg.solve(big, b)[:n].reshape(rhs.shape)
 
 
-def var_coeff_solve_dense(rhs, rho, lengths, rule=FACE_ARITHMETIC):
-    """Zero-mean q with D[(1/rho_f) G q] = rhs (Eq. (30)) by dense LU: small grids."""
-    mat = dense_operator(lambda q: var_coeff_apply(q, rho, lengths, rule), rho.shape)
+def var_coeff_solve_dense(rhs, rho, lengths, rule=FACE_ARITHMETIC, bc_top=BC_WALL):
+    """q with D[(1/rho_f) G q] = rhs (Eq. (30)) by dense LU (small grids): the
+    zero-mean solution for walls, the unique one for an outflow top."""
+    mat = dense_operator(lambda q: var_coeff_apply(q, rho, lengths, rule, bc_top), rho.shape)
+    if bc_top == BC_OUTFLOW:
+        return np.linalg.solve(mat, rhs.ravel()).reshape(rhs.shape)
     return dense_zero_mean_solve(mat, rhs)
 
 

@@ -279,7 +279,7 @@ def test_planted_sign_mistake_is_caught(monkeypatch):
 
 def test_planted_split_mistake_is_caught(monkeypatch):
     """Dropping the explicit split term of Eq. (34) must fail split exactness."""
-    def bad(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=O.FACE_ARITHMETIC):
+    def bad(u, v, w, S, rho, p_n, p_nm1, rho0, dt, lengths, rule=O.FACE_ARITHMETIC, bc_top=O.BC_WALL):
         h = O.spacings(rho.shape, lengths)
         return (rho0 / dt) * (O.div(u, v, w, h) - S)
     fl = _fields(n=(8, 6, 10), seed=9, width=2.0)
@@ -426,3 +426,86 @@ def test_planted_phase_change_sign_is_caught(monkeypatch):
     z = np.zeros_like(C)
     Se, _ = O.divergence_constraint(np.full_like(C, 0.5), z, z, np.ones_like(C), rg, rl)
     assert not np.all(Se > 0.0)
+
+
+
+# ---------------------------------------------------------------------------
+# outflow top boundary (p = 0 on the face y = Ly; the bottom stays a wall)
+# ---------------------------------------------------------------------------
+OUT = O.BC_OUTFLOW
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 4), (8, 7, 6)])
+@pytest.mark.parametrize("abc", [(0, 0, 0), (1, 3, 2), (2, 0, 1)])
+def test_outflow_eigenfunction_manufactured(shape, abc):
+    """DCT-IV modes cos(pi (b + 1/2)(j + 1/2)/Ny) times Fourier modes in x, z
+    are eigenfunctions of the 7-point operator with the outflow ghost value;
+    the solve inverts them (including a = b = c = 0, which is no zero mode)."""
+    nz, ny, nx = shape
+    a, b, c = abc
+    h = O.spacings(shape, LENGTHS)
+    x = (np.arange(nx) + 0.5) * h[0]
+    z = (np.arange(nz) + 0.5) * h[2]
+    phi = (np.cos(2 * math.pi * a * x / LENGTHS[0] + 0.4)[None, None, :]
+           * np.cos(math.pi * (b + 0.5) * (np.arange(ny) + 0.5) / ny)[None, :, None]
+           * np.cos(2 * math.pi * c * z / LENGTHS[2] - 0.7)[:, None, None])
+    lam = (-(4 / h[0] ** 2) * math.sin(math.pi * a / nx) ** 2
+           - (4 / h[1] ** 2) * math.sin(math.pi * (b + 0.5) / (2 * ny)) ** 2
+           - (4 / h[2] ** 2) * math.sin(math.pi * c / nz) ** 2)
+    assert np.max(np.abs(O.laplacian(phi, h, OUT) - lam * phi)) < 1e-10 * abs(lam)
+    assert O.rel_linf(O.ppe_solve(lam * phi, LENGTHS, OUT), phi) < 1e-12
+
+
+def test_outflow_laplacian_brute_force_and_dense():
+    """The top cell sees the ghost value -p_{Ny-1} (p = 0 on the face); the
+    spectral solve equals a dense LU solve of the 7-point operator."""
+    shape = (6, 5, 8)
+    nz, ny, nx = shape
+    h = O.spacings(shape, LENGTHS)
+    q = np.random.default_rng(3).standard_normal(shape)
+    lap = O.laplacian(q, h, OUT)
+    for (k, j, i) in [(0, ny - 1, 0), (3, ny - 1, 5), (2, 0, 7), (5, 2, 3)]:
+        up = q[k, j + 1, i] if j + 1 < ny else -q[k, j, i]
+        dn = q[k, j - 1, i] if j > 0 else q[k, j, i]
+        ref = ((q[k, j, (i + 1) % nx] - 2 * q[k, j, i] + q[k, j, i - 1]) / h[0] ** 2
+               + (up - 2 * q[k, j, i] + dn) / h[1] ** 2
+               + (q[(k + 1) % nz, j, i] - 2 * q[k, j, i] + q[k - 1, j, i]) / h[2] ** 2)
+        assert abs(ref - lap[k, j, i]) < 1e-12 * np.max(np.abs(lap))
+    f = np.random.default_rng(4).standard_normal(shape) + 3.0  # any mean: nothing is dropped
+    mat = O.dense_operator(lambda p: O.laplacian(p, h, OUT), shape)
+    dense = np.linalg.solve(mat, f.ravel()).reshape(shape)
+    assert O.rel_linf(O.ppe_solve(f, LENGTHS, OUT), dense) < 1e-12
+
+
+@pytest.mark.parametrize("rule", [O.FACE_ARITHMETIC, O.FACE_HARMONIC])
+def test_outflow_divergence_identity_and_split_exactness(rule):
+    """With an open top, D u^{n+1} = S holds for any S (no compatibility
+    condition), the top-face velocity is corrected, and O7 holds: with
+    p^n = p^{n-1} = q solving the unsplit Eq. (30) the split returns q."""
+    fl = _fields(n=(8, 6, 10), seed=12, width=2.0)
+    h = O.spacings(fl.shape, LENGTHS)
+    S = fl.S + 0.3  # a net expansion, which walls could not absorb
+    out = O.ppe_project(fl.u, fl.v, fl.w, S, fl.rho, fl.p_n, fl.p_nm1, fl.dt, LENGTHS, rule=rule, bc_top=OUT)
+    div_new = O.div(out["u"], out["v"], out["w"], h)
+    assert np.max(np.abs(div_new - S)) < 1e-11 * np.max(np.abs(O.div(fl.u, fl.v, fl.w, h)))
+    assert np.all(out["v"][:, 0, :] == fl.v[:, 0, :])
+    assert not np.allclose(out["v"][:, -1, :], fl.v[:, -1, :])
+    src = (O.div(fl.u, fl.v, fl.w, h) - S) / fl.dt
+    q = O.var_coeff_solve_dense(src, fl.rho, LENGTHS, rule, OUT)
+    out2 = O.ppe_project(fl.u, fl.v, fl.w, S, fl.rho, q, q, fl.dt, LENGTHS, rule=rule, bc_top=OUT)
+    assert O.rel_linf(out2["p"], q) < 1e-11
+
+
+def test_planted_outflow_eigenvalue_mistake_is_caught(monkeypatch):
+    """Solving the outflow problem with the wall (DCT-II) eigenvalues must fail
+    the manufactured eigenfunction."""
+    good = O.eigenvalues
+    monkeypatch.setattr(O, "eigenvalues", lambda shape, lengths, bc_top=O.BC_WALL: good(shape, lengths))
+    shape = (6, 5, 4)
+    nz, ny, nx = shape
+    h = O.spacings(shape, LENGTHS)
+    phi = np.broadcast_to(np.cos(math.pi * 1.5 * (np.arange(ny) + 0.5) / ny)[None, :, None], shape).copy()
+    lam = -(4 / h[1] ** 2) * math.sin(math.pi * 1.5 / (2 * ny)) ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):  # the wall table has a zero eigenvalue
+        err = O.rel_linf(O.ppe_solve(lam * phi, LENGTHS, OUT), phi)
+    assert not err < 1e-3
