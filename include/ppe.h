@@ -76,8 +76,18 @@ typedef enum { PPE_FP64 = 0, PPE_FP32_REFINE = 1 } ppe_precision;
  * interface quantities only; the density rule is a reading of it. */
 typedef enum { PPE_FACE_ARITHMETIC = 0, PPE_FACE_HARMONIC = 1 } ppe_face_rule;
 
+/* Top boundary in y (y = ly); the bottom (y = 0) is always a wall.
+ * PPE_BC_WALL: no penetration, homogeneous Neumann for p (the default).
+ * PPE_BC_OUTFLOW: an open boundary as in the paper's jet cases (Sec. 6): p = 0
+ * on the top face, imposed through the ghost value p_ny = -p_{ny-1}; the top
+ * face's v is corrected like an interior face (face density: the top cell's),
+ * there is no zero mode and no compatibility condition on S, and the y solve
+ * is tridiagonal in both precisions.  Not supported by ppe_project_unsplit. */
+typedef enum { PPE_BC_WALL = 0, PPE_BC_OUTFLOW = 1 } ppe_bc;
+
 /* Uniform grid, nx x ny x nz cells in a box lx x ly x lz; periodic in x and z,
- * walls (no penetration, homogeneous Neumann for p) at y = 0 and y = ly. */
+ * a wall (no penetration, homogeneous Neumann for p) at y = 0 and, by
+ * default, at y = ly (see ppe_bc). */
 typedef struct {
     int nx, ny, nz;
     double lx, ly, lz;
@@ -97,6 +107,7 @@ typedef struct {
                          * when |mean(f)| > compat_tol * ||f||_inf.  0: no check.  The
                          * paper has no such check; it follows from the divergence
                          * theorem on the periodic/wall box of Sec. 5. */
+    ppe_bc bc_top;      /* top boundary in y (PPE_BC_WALL when opt is NULL) */
 } ppe_options;
 
 /* Read back by ppe_get_info after a solve or projection. */
@@ -108,7 +119,7 @@ typedef struct {
     /* Compatibility of the last assembled right-hand side (NaN if no ppe_rhs /
      * ppe_project ran since the plan was made).  f_mean_removed and s_mean need
      * the sum of f, which the solve forms: after ppe_rhs alone they are NaN. */
-    double s_mean;          /* mean of S over the cells, from the divergence theorem:
+    double s_mean;          /* (walls only; NaN with an open top) mean of S over the cells, from the divergence theorem:
                              * sum over cells of D u* keeps only the wall faces and
                              * sum D(beta G p_hat) = 0, so by Eq. (34)
                              * mean(S) = wall_flux_mean - (dt/rho_0) mean(f) */

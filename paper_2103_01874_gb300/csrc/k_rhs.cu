@@ -226,7 +226,12 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
             const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
             const df vs = d2df(vv[u]);
             const bool own = (jf < tj) || (j == ny);
-            if (j == 0 || j == ny) {
+            if (j == ny && g.top_open) {  // open top: p = 0 on the face, ghost -p_hat above
+              const int rl = jf * nx + i;
+              const FaceOut fo = face_q(R[rl], R[rl], P[rl], df_neg(P[rl]), vs, K.cy, K.gy, K, rule);
+              q = fo.q;
+              if (PROJ && own) out.vpre[cvv] = fo.upre;
+            } else if (j == 0 || j == ny) {  // wall
               q = df_norm(df_mulz(K.cy, vs));
               if (PROJ && own) out.vpre[cvv] = vs;
               wsum = (j == ny) ? df_addz(wsum, vs) : df_subz(wsum, vs);
@@ -489,7 +494,13 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       // a face belongs to the stack holding the line above it; the top wall to
       // the stack holding line ny - 1
       const bool own = (f < S && j < ny) || (j == ny && f >= 1);
-      if (j == 0 || j == ny) {
+      if (j == ny && g.top_open) {  // open top: p = 0 on the face, ghost -p_hat above
+        const df rl = (f == 0) ? R[(jb) * nx + i] : RC[f > 0 ? f - 1 : 0];
+        const df pl = (f == 0) ? P[(jb) * nx + i] : PC[f > 0 ? f - 1 : 0];
+        const FaceOut fo = face_q(rl, rl, pl, df_neg(pl), vs, K.cy, K.gy, K, rule);
+        QY[f] = fo.q;
+        if (PROJ && own) out.vpre[cvv] = fo.upre;
+      } else if (j == 0 || j == ny) {  // wall
         QY[f] = df_norm(df_mulz(K.cy, vs));
         if (PROJ && own) out.vpre[cvv] = vs;
         if (own) {

@@ -77,7 +77,8 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 // ---------------------------------------------------------------------------
 // forward x pass
 // ---------------------------------------------------------------------------
-template <typename T, int SRC, bool DO_FFT, int N>
+// OPEN: the residual's top cells see the outflow ghost (SRC_RESID only)
+template <typename T, int SRC, bool DO_FFT, int N, bool OPEN = false>
 __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
                                               const df* __restrict__ pdf, cpx<T>* spec, RadixPlan rp,
                                               const cpx<T>* __restrict__ tw, int lpb) {
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
           pxm[u] = pdf[(i == 0) ? c + nx - 1 : c - 1];
           pzp[u] = pdf[(k + 1 == nzu) ? c - (nzu - 1) * plane : c + plane];
           pzm[u] = pdf[(k == 0) ? c + (nzu - 1) * plane : c - plane];
-          pyp[u] = (j + 1 < (uint32_t)g.ny) ? pdf[c + nx] : pc[u];
+          // above the top cell: the wall mirror, or the outflow ghost -p (p = 0 on the face)
+          pyp[u] = (j + 1 < (uint32_t)g.ny) ? pdf[c + nx] : (OPEN ? df_neg(pc[u]) : pc[u]);
           pym[u] = (j > 0) ? pdf[c - nx] : pc[u];
           fv[u] = fdf[c];
         }
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const 
   const int c = threadIdx.x;
   if (c < tl && kx0 + c < nxh) {
     const T* m = tm + c * (ny + 1);
-    const bool zero_line = (kz == 0 && kx0 + c == 0);
+    const bool zero_line = !g.top_open && kz == 0 && kx0 + c == 0;  // the wall problem's singular line
     cpx<T> shift = {(T)0, (T)0};
     if (zero_line) {
       double sx = 0.0, sy = 0.0;
@@ -559,12 +561,18 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
     } else if (src == SRC_FDF) {
       if ((e = allow_smem(k_xfwd<T, SRC_FDF, true, N>, sm)) != cudaSuccess) return e;
       k_xfwd<T, SRC_FDF, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-    } else if (do_fft) {
+    } else if (do_fft && !g.top_open) {
       if ((e = allow_smem(k_xfwd<T, SRC_RESID, true, N>, sm)) != cudaSuccess) return e;
       k_xfwd<T, SRC_RESID, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
-    } else {
+    } else if (do_fft) {
+      if ((e = allow_smem(k_xfwd<T, SRC_RESID, true, N, true>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_RESID, true, N, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    } else if (!g.top_open) {
       if ((e = allow_smem(k_xfwd<T, SRC_RESID, false, 0>, sm)) != cudaSuccess) return e;
       k_xfwd<T, SRC_RESID, false, 0><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
+    } else {
+      if ((e = allow_smem(k_xfwd<T, SRC_RESID, false, 0, true>, sm)) != cudaSuccess) return e;
+      k_xfwd<T, SRC_RESID, false, 0, true><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
     }
     return cudaGetLastError();
   });

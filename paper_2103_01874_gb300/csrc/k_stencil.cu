@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(256) k_correct_pre(GridDev g, double dt, const
         pxm[u] = P(n.xm);
         pzm[u] = P(n.zm);
         pym[u] = (j > 0) ? P(n.c - nx) : p0[u];
+      } else if (g.top_open) {
+        p0[u] = P(((size_t)k * ny + (ny - 1)) * nx + i);  // the top cell below the open face
       }
     }
 #pragma unroll
@@ -102,6 +104,10 @@ __global__ void __launch_bounds__(256) k_correct_pre(GridDev g, double dt, const
       const int j = jj[u];
       if (j < 0) continue;
       const uint32_t t = t0 + u * stride;
+      if (j == (int)ny && g.top_open) {  // open top: the ghost -p of the cell below
+        v_out[t] = df2d(df_subz(vp[u], df_mulz(K.gy, df_subz(df_neg(p0[u]), p0[u]))));
+        continue;
+      }
       if (j == 0 || j == (int)ny) {
         v_out[t] = df2d(vp[u]);
         if (j == (int)ny) continue;
@@ -131,6 +137,15 @@ __global__ void __launch_bounds__(256) k_correct_full(GridDev g, StencilIn in, c
     const int k = (int)fdiv(r, g.fd_nyp1);
     const int j = (int)(r - (uint32_t)k * (uint32_t)(ny + 1));
     const size_t cv = t;
+    if (j == g.ny && g.top_open) {
+      // open top: the face between the top cell and its ghost (-p, -p_hat, same density)
+      const size_t ct = ((size_t)k * ny + (ny - 1)) * nx + i;
+      const df pt = d2df(in.p[ct]), ht = phat_df(in.pn, in.pnm1, ct), rt = d2df(__ldg(in.rho + ct));
+      const df b = beta_df(rt, rt, K, rule);
+      const df gp = df_subz(df_neg(pt), pt), gh = df_subz(df_neg(ht), ht);
+      v_out[cv] = df2d(df_subz(d2df(in.v[cv]), df_mulz(K.gy, df_subz(gp, df_mulz(b, gh)))));
+      continue;
+    }
     if (j == 0 || j == g.ny) {
       v_out[cv] = in.v[cv];
       if (j == g.ny) continue;
@@ -202,7 +217,8 @@ __global__ void k_set_outputs(DevScalars* sc, double* p, double* u, double* v, d
 // r = f - L p of that same p at every cell (max into rmax[iter + 1]), so that the
 // convergence test after a correction needs no separate pass.
 // SUB: the mean of f is non-zero and is left out of the residual (the solve drops it)
-template <bool SUB>
+// OPEN: outflow top (the top face is corrected, the top cells see the ghost -p)
+template <bool SUB, bool OPEN>
 __device__ __forceinline__ void correct_check_body(const GridDev& g, const df* __restrict__ upre,
                                                    const df* __restrict__ vpre, const df* __restrict__ wpre,
                                                    const df* __restrict__ pdf, const df* __restrict__ fdf,
@@ -226,8 +242,13 @@ __device__ __forceinline__ void correct_check_body(const GridDev& g, const df* _
     const uint32_t k = fdiv(r, g.fd_nyp1);
     const uint32_t j = r - k * (ny + 1);
     const df vp = vpre[t];
-    if (j == ny) {  // upper wall: v unchanged
-      v_out[t] = df2d(vp);
+    if (j == ny) {  // top face: a wall keeps v; an open top sees the ghost -p of the cell below
+      if (OPEN) {
+        const df pt = pdf[k * plane + (ny - 1) * nx + i];  // the top cell (i, ny-1, k)
+        v_out[t] = df2d(df_subz(vp, df_mulz(K.gy, df_subz(df_neg(pt), pt))));
+      } else {
+        v_out[t] = df2d(vp);
+      }
       continue;
     }
     const uint32_t c = k * plane + j * nx + i;
@@ -238,7 +259,7 @@ __device__ __forceinline__ void correct_check_body(const GridDev& g, const df* _
     const df up = upre[c], wp = wpre[c], q = pdf[c];
     const df pxm = pdf[xm], pxp = pdf[xp], pzm = pdf[zm], pzp = pdf[zp];
     const df pym = (j > 0) ? pdf[c - nx] : q;
-    const df pyp = (j + 1 < ny) ? pdf[c + nx] : q;
+    const df pyp = (j + 1 < ny) ? pdf[c + nx] : (OPEN ? df_neg(q) : q);
     const df fv = fdf[c];
     // backward differences (the faces of this cell) serve Eq. (33) and the residual
     const df dxm = df_subz(q, pxm), dym = df_subz(q, pym), dzm = df_subz(q, pzm);
@@ -261,10 +282,12 @@ __global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* _
                                                        const df* __restrict__ pdf, const df* __restrict__ fdf,
                                                        DevScalars* sc) {
   const df fmean = sc->f_mean;
-  if (fmean.hi == 0.0f)
-    correct_check_body<false>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
+  if (g.top_open)
+    correct_check_body<false, true>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);  // no mean is left out
+  else if (fmean.hi == 0.0f)
+    correct_check_body<false, false>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
   else
-    correct_check_body<true>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
+    correct_check_body<true, false>(g, upre, vpre, wpre, pdf, fdf, sc, fmean);
 }
 
 __global__ void k_make_const(GridDev g, DevScalars* sc, double dt) {

@@ -178,10 +178,14 @@ ppe_status make_thomas(ppe_plan_t P) {
     for (int kx = 0; kx < nxh; ++kx) {
       const double sx = sin_pi_frac(kx, nx);
       const double lam = -(4.0 / (dx * dx)) * sx * sx + lz;
-      const bool zero = (kx == 0 && kz == 0);
+      // walls: the kx = kz = 0 line is singular and pinned by the kernel; an open
+      // top (ghost -p above the last cell) makes the last diagonal -3a + lam
+      // and every line regular
+      const bool open = P->gd.top_open != 0;
+      const bool zero = !open && kx == 0 && kz == 0;
       m[0] = zero ? 0.0 : 1.0 / (-a + lam);
       for (int j = 1; j < ny - 1; ++j) m[j] = 1.0 / ((-2.0 * a + lam) - a * (a * m[j - 1]));
-      m[ny - 1] = 1.0 / ((-a + lam) - a * (a * m[ny - 2]));
+      m[ny - 1] = 1.0 / (((open ? -3.0 : -1.0) * a + lam) - a * (a * m[ny - 2]));
       for (int j = 0; j < ny; ++j) mt[j] = (T)m[j];
       int J = ny - 1;  // entries m_0 .. m_{J-1} stored; m_j == m_{ny-2} for J <= j <= ny-2
       while (J > 0 && mt[J - 1] == mt[ny - 2]) --J;
@@ -331,7 +335,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   DevScalars* fin = guarded ? nullptr : P->sc;
   PPE_LAUNCH(P, K_ZFFT_FWD,
              launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, fin, P->stream));
-  if (P->fp32) {
+  if (P->fp32 && !P->gd.top_open) {  // DCT-II/III for walls; the open top uses the tridiagonal solve
     const T* lam = (const T*)P->lam;
     PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
                                             lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->stream));
@@ -679,12 +683,14 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   o.refine_tol = 1e-10;
   o.max_sweeps = 6;
   o.compat_tol = 1e-12;
+  o.bc_top = PPE_BC_WALL;
   if (opt) o = *opt;
   if (o.precision != PPE_FP64 && o.precision != PPE_FP32_REFINE) return PPE_ERR_INVALID_ARG;
   if (o.face_rule != PPE_FACE_ARITHMETIC && o.face_rule != PPE_FACE_HARMONIC) return PPE_ERR_INVALID_ARG;
   if (o.max_sweeps < 0 || o.max_sweeps > kMaxSweeps) return PPE_ERR_INVALID_ARG;
   if (o.precision == PPE_FP32_REFINE && !(o.refine_tol >= 0)) return PPE_ERR_INVALID_ARG;
   if (!(o.compat_tol >= 0)) return PPE_ERR_INVALID_ARG;
+  if (o.bc_top != PPE_BC_WALL && o.bc_top != PPE_BC_OUTFLOW) return PPE_ERR_INVALID_ARG;
 
   ppe_plan_t P = new (std::nothrow) ppe_plan_s;
   if (!P) return PPE_ERR_OUT_OF_MEMORY;
@@ -705,6 +711,7 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->gd.nx = g->nx;
   P->gd.ny = g->ny;
   P->gd.nz = g->nz;
+  P->gd.top_open = o.bc_top == PPE_BC_OUTFLOW ? 1 : 0;
   P->gd.idx = g->nx / g->lx;
   P->gd.idy = g->ny / g->ly;
   P->gd.idz = g->nz / g->lz;
@@ -743,7 +750,7 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
     if (P->fp32) {
       s = make_twiddles<float>(&P->tw_x, g->nx);
       if (s == PPE_OK) s = make_twiddles<float>(&P->tw_z, g->nz);
-      if (s == PPE_OK) s = make_dct_tables<float>(P);
+      if (s == PPE_OK) s = P->gd.top_open ? make_thomas<float>(P) : make_dct_tables<float>(P);
       if (s == PPE_OK) s = cuda_status(set_smem_limits<float>());
     } else {
       s = make_twiddles<double>(&P->tw_x, g->nx);
@@ -969,6 +976,7 @@ ppe_status ppe_project_unsplit(ppe_plan_t P, const ppe_fields* F, double tol, in
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
   PPE_TRY(cudaStreamIsCapturing(P->stream, &cst));
   if (cst != cudaStreamCaptureStatusNone) return PPE_ERR_INVALID_ARG;  // not capturable
+  if (P->gd.top_open) return PPE_ERR_INVALID_ARG;  // the unsplit baseline has walls only
   ppe_status s = ensure_vc(P);
   if (s != PPE_OK) return s;
   if (!P->pcg_exec && (s = build_pcg_graph(P)) != PPE_OK) return s;
@@ -1179,10 +1187,12 @@ ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
     // Over the cells, sum D u* = sum over (i, k) of (v*(ny) - v*(0)) / dy (x, z
     // periodic) and sum D(beta G p_hat) = 0 (G = 0 on the walls), so by Eq. (34)
     // mean(S) = wall_flux_mean - (dt/rho_0) mean(f).
-    if (h.f_ran) info->s_mean = info->wall_flux_mean - info->f_mean_removed / df2d(h.K.c);
+    // (walls only: an open top face carries flux of both terms)
+    if (h.f_ran && !P->gd.top_open) info->s_mean = info->wall_flux_mean - info->f_mean_removed / df2d(h.K.c);
   }
   // the Neumann problem needs mean(f) = 0; what the solve drops, relative to ||f||
-  if (h.f_ran && P->opt.compat_tol > 0) incompatible = fabs(h.f_sum / n) > P->opt.compat_tol * fmax;
+  // (an open top has no compatibility condition)
+  if (h.f_ran && P->opt.compat_tol > 0 && !P->gd.top_open) incompatible = fabs(h.f_sum / n) > P->opt.compat_tol * fmax;
   if (P->fp32) {
     info->sweeps = h.sweeps;
     if (h.last_slot >= 0 && fmax > 0)

@@ -70,6 +70,7 @@ struct DevScalars {
 
 struct GridDev {
   int nx, ny, nz;
+  int top_open;          // 1: outflow top (p = 0 on the face y = Ly, ghost p_ny = -p_{ny-1}); 0: wall
   double idx, idy, idz;  // 1/dx, 1/dy, 1/dz
   FastDiv fd_nx, fd_nxh, fd_m, fd_ny, fd_nyp1;  // dividers by nx, nx/2+1, nx/2, ny, ny+1
 };

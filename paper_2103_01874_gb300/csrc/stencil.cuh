@@ -189,7 +189,8 @@ __device__ __forceinline__ void finish_sums(DevScalars* sc, const GridDev& g) {
     const double mean = fs / ((double)g.nx * (double)g.ny * (double)g.nz);
     const double fmax = __longlong_as_double((long long)sc->fmax_bits);
     sc->f_sum = fs;
-    sc->f_mean = (fabs(mean) > 0x1p-40 * fmax) ? d2df(mean) : df{0.0f, 0.0f};
+    // (an open top has no zero mode: nothing is dropped, nothing left out)
+    sc->f_mean = (!g.top_open && fabs(mean) > 0x1p-40 * fmax) ? d2df(mean) : df{0.0f, 0.0f};
     sc->f_ran = 1;
   }
 }

@@ -22,6 +22,8 @@ FP64 = 0
 FP32_REFINE = 1
 FACE_ARITHMETIC = 0
 FACE_HARMONIC = 1
+BC_WALL = 0      # top boundary in y: wall (ppe_bc)
+BC_OUTFLOW = 1   # open top, p = 0 on the face
 
 STATUS = {0: "PPE_OK", 1: "PPE_ERR_INVALID_ARG", 2: "PPE_ERR_UNSUPPORTED_SIZE", 3: "PPE_ERR_INCOMPATIBLE_RHS",
           4: "PPE_ERR_OUT_OF_MEMORY", 5: "PPE_ERR_NOT_CONVERGED", 6: "PPE_ERR_TIMEOUT", 7: "PPE_ERR_CUDA"}
@@ -39,7 +41,7 @@ class Grid(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("face_rule", c_int), ("refine_tol", c_double), ("max_sweeps", c_int),
-                ("compat_tol", c_double)]
+                ("compat_tol", c_double), ("bc_top", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -237,12 +239,14 @@ class Plan:
     """A libppe plan for one grid (ppe_plan / ppe_destroy)."""
 
     def __init__(self, nx, ny, nz, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi, precision=FP64,
-                 face_rule=FACE_ARITHMETIC, refine_tol=1e-10, max_sweeps=6, stream=None, compat_tol=1e-12):
+                 face_rule=FACE_ARITHMETIC, refine_tol=1e-10, max_sweeps=6, stream=None, compat_tol=1e-12,
+                 bc_top=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.lengths = (lx, ly, lz)
         self.precision = precision
         self.grid = Grid(nx, ny, nz, lx, ly, lz)
-        self.opts = Options(precision, face_rule, refine_tol, max_sweeps, compat_tol)
+        self.bc_top = BC_WALL if bc_top is None else bc_top
+        self.opts = Options(precision, face_rule, refine_tol, max_sweeps, compat_tol, self.bc_top)
         h = c_void_p()
         _check(lib().ppe_plan(ctypes.byref(h), ctypes.byref(self.grid), ctypes.byref(self.opts),
                               c_void_p(_stream_handle(stream))), "ppe_plan")
