@@ -192,20 +192,22 @@ PPE_HD df df_recipz(df a) {
 }
 
 // IEEE double -> pair (see header comment).  Relative error <= 2^-48.
+// hi: the 9 bits below the sign of (hw << 3 | lw >> 29) hold the exponent
+// modulo 512 and the top 23 mantissa bits follow, so adding 128 << 23
+// rebiases 1023 -> 127 (modulo 512) for every in-range exponent and the sign
+// is or-ed back.  lo: the 29 low mantissa bits, converted once, times
+// 2^(e - 1075) = 2^(E_hi - 52), whose bit pattern (with the sign of x) is hi's
+// sign and exponent field minus 52 << 23.  |x| < 2^-74 gives (0, 0).
 PPE_HD df d2df(double x) {
   const uint64_t b = d_bits(x);
   const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
-  const uint32_t e = (hw >> 20) & 0x7FFu;
-  const uint32_t sign = hw & 0x80000000u;
-  // hi: rebias 1023 -> 127 and keep the top 23 mantissa bits
-  const uint32_t hb = sign | (((hw & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lw >> 29);
-  // lo: 29 low mantissa bits times 2^(e - 1075)
-  const float m = (float)(lw & 0x1FFFFFFFu);
-  const float sc = f_from((e - 948u) << 23);
-  const float lo = f_from(f_bits(m * sc) | sign);
+  const uint32_t hb = (((hw << 3) | (lw >> 29)) + 0x40000000u) | (hw & 0x80000000u);
+  const float sc = f_from((hb & 0xFF800000u) - 0x1A000000u);
+  const float lo = (float)(lw & 0x1FFFFFFFu) * sc;
+  const bool ok = (hw & 0x7FF00000u) >= (949u << 20);
   df r;
-  r.hi = (e >= 897u) ? f_from(hb) : 0.0f;
-  r.lo = (e >= 949u) ? lo : 0.0f;
+  r.hi = ok ? f_from(hb) : 0.0f;
+  r.lo = ok ? lo : 0.0f;
   return r;
 }
 

@@ -20,11 +20,15 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fastdiv.cuh"
 
 namespace ppe {
 
-template <typename T> struct cpx { T x, y; };
+// Aligned to its full size, so that one element moves with one 8-byte (FP32) or
+// 16-byte (FP64) access.
+template <typename T> struct alignas(2 * sizeof(T)) cpx { T x, y; };
 
 template <typename T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
@@ -310,5 +314,101 @@ __device__ __forceinline__ cpx<T>* fft_lines_ct(cpx<T>* a, cpx<T>* b, int nl_log
                                                 const cpx<T>* __restrict__ tw) {
   return ctfft::run_from<T, INV, N, 0, MAXR, TWS>(a, b, nl_log2, ls, es, tw);
 }
+
+
+// ---------------------------------------------------------------------------
+// Register-staged variant for power-of-two lengths 16 <= N <= 512 (FP32
+// lines).  Each line is transformed by TPL = N/16 threads; between passes a
+// thread keeps 16 elements in registers, so a pass costs one shared-memory
+// store and one load per element, and there is no separate staging copy: the
+// first pass takes its butterfly inputs from a caller functor `ld(e)` (global
+// memory, values computed on the fly, or the shared buffer) and the last pass
+// hands its outputs to `st(e, v)`.  Radix sequence, twiddles and butterflies
+// are those of fft_lines_ct.
+//
+// Shared layout: element e of the thread's line at ln[row(e) * es], ln the
+// line's base; row(e) = e + e/16 inserts one padding row every 16 elements,
+// so that the strided writes of the first pass (rows 16 t + q for the t of a
+// warp) fall on different banks.  Lines across columns (z and y passes: lines
+// fastest, es = lines per CTA) or along rows (x passes: es = 1, line stride
+// chosen by the caller).
+// ---------------------------------------------------------------------------
+namespace rgfft {
+
+__host__ __device__ constexpr int rows(int n) { return n + n / 16; }
+__device__ __forceinline__ int row(int e) { return e + (e >> 4); }
+
+// LD_SHARED: ld reads the shared buffer (the first pass then waits for all
+// reads before writing); later passes always read all before their stores.
+template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, class Ld, class St>
+__device__ __forceinline__ void pass(Ld& ld, St& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
+  using namespace ctfft;
+  constexpr int NST = nst(N, 16);
+  constexpr int R = radix_at(N, S, 16);
+  constexpr int NS = ns_at(N, S, 16);
+  constexpr int NB = N / R;
+  constexpr int TPL = N / 16;
+  constexpr int IT = NB / TPL;
+  constexpr int TSTEP = N / (NS * R);
+  static_assert(IT * R == 16, "a thread holds 16 elements per pass");
+  cpx<T> v[IT][R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int t = t0 + it * TPL;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int e = t + q * NB;
+      if (S == 0) v[it][q] = ld(e);
+      else v[it][q] = ln[row(e) * es];
+    }
+  }
+  if (S > 0 || LD_SHARED) __syncthreads();  // in place: every read of the pass before any write
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int t = t0 + it * TPL;
+    const int q0 = t / NS, k = t - q0 * NS;
+    if (NS > 1) {
+      const int e1 = TSTEP * TWS * k;
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        cpx<T> w = tw[q * e1];
+        if (INV) w.y = -w.y;
+        v[it][q] = cmul(v[it][q], w);
+      }
+    }
+    SmallDft<T, INV, R>::run(v[it]);
+    const int o = q0 * NS * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (S + 1 == NST) st(o + q * NS, v[it][q]);
+      else ln[row(o + q * NS) * es] = v[it][q];
+    }
+  }
+  if (S + 1 < NST) __syncthreads();
+}
+
+template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, class Ld, class St>
+__device__ __forceinline__ void run_from(Ld& ld, St& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
+  if constexpr (S < ctfft::nst(N, 16)) {
+    pass<T, INV, N, S, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
+    run_from<T, INV, N, S + 1, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
+  }
+}
+
+// Transform of the CTA's lines (N/16 threads per line, every thread of the
+// CTA calls; t0 in [0, N/16) is the thread's rank within its line).  `tw`
+// holds exp(-2 pi i t/(N*TWS)) and must be visible to all threads before the
+// second pass (the barrier after the first pass suffices when it is written
+// before the call).  The caller synchronises after the call before reusing
+// the buffer.
+template <typename T, bool INV, int N, int TWS, bool LD_SHARED, class Ld, class St>
+__device__ __forceinline__ void run(Ld&& ld, St&& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
+  static_assert((N & (N - 1)) == 0 && N >= 16 && N <= 512, "power-of-two length");
+  run_from<T, INV, N, 0, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
+}
+
+template <int N> struct is_rg : std::integral_constant<bool, (N >= 16 && N <= 512 && (N & (N - 1)) == 0)> {};
+
+}  // namespace rgfft
 
 }  // namespace ppe

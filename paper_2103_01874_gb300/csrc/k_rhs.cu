@@ -11,8 +11,9 @@
 // and this kernel stores u_pre_f = u*_f + (dt/rho_0) beta_f (G p_hat)_f, leaving
 // only the pressure-gradient term for the kernel that runs after the solve.
 //
-// Arithmetic: FP64 inputs are split into float pairs with integer operations
-// (dfloat.cuh) and every face and cell value is formed in pair arithmetic.
+// Arithmetic: p_hat is formed by one FP64 fused multiply-add; it and the other
+// FP64 inputs are split into float pairs with integer operations (dfloat.cuh)
+// and every face and cell value is formed in pair arithmetic.
 //
 // Blocking: a CTA owns `tj` consecutive y-lines for a chunk of `kc` z-planes and
 // marches upward in z.  Each thread owns fixed (i, j) columns of the tile and
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
     }
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
-      pv[u] = df_sub(df_ldexp2(d2df(a[u])), d2df(b[u]));  // p_hat = 2 p^n - p^{n-1}
+      pv[u] = phat_of(a[u], b[u]);  // p_hat = 2 p^n - p^{n-1}
       rv[u] = d2df(r[u]);
     }
   };
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       df pv = {0.0f, 0.0f}, rv = {1.0f, 0.0f};
       if (j >= 0 && j < ny) {
         const uint32_t c = cell(kk, j, i);
-        pv = df_sub(df_ldexp2(d2df(__ldg(in.pn + c))), d2df(__ldg(in.pnm1 + c)));
+        pv = phat_of(__ldg(in.pn + c), __ldg(in.pnm1 + c));
         rv = d2df(__ldg(in.rho + c));
       }
       P[l * nx + i] = pv;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 
       load_halo(k + 1);
 #pragma unroll
       for (int u = 0; u < CPT; ++u) {
-        P1[u] = df_sub(df_ldexp2(d2df(rp[u])), d2df(rm[u]));
+        P1[u] = phat_of(rp[u], rm[u]);
         R1[u] = d2df(rr[u]);
       }
       __syncthreads();
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     }
 #pragma unroll
     for (int l = 0; l < S; ++l) {
-      pv[l] = df_sub(df_ldexp2(d2df(a[l])), d2df(b[l]));  // p_hat = 2 p^n - p^{n-1}
+      pv[l] = phat_of(a[l], b[l]);  // p_hat = 2 p^n - p^{n-1}
       rv[l] = d2df(r[l]);
     }
   };
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       df pv = {0.0f, 0.0f}, rv = {1.0f, 0.0f};
       if (j >= 0 && j < ny) {
         const uint32_t c = (uint32_t)kk * plane + (uint32_t)(j * nx + x);
-        pv = df_sub(df_ldexp2(d2df(__ldg(in.pn + c))), d2df(__ldg(in.pnm1 + c)));
+        pv = phat_of(__ldg(in.pn + c), __ldg(in.pnm1 + c));
         rv = d2df(__ldg(in.rho + c));
       }
       P[row * nx + x] = pv;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       load_halo(k + 1);
 #pragma unroll
       for (int l = 0; l < S; ++l) {
-        P1[l] = df_sub(df_ldexp2(d2df(rp[l])), d2df(rm[l]));
+        P1[l] = phat_of(rp[l], rm[l]);
         R1[l] = d2df(rr[l]);
       }
       __syncthreads();

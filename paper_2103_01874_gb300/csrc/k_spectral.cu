@@ -225,6 +225,132 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
   }
 }
 
+// Line stride (complex elements) of the x passes' shared buffer: rgfft rows,
+// padded to 8 mod 16 so that neighbouring lines start half a bank row apart.
+__host__ __device__ constexpr int xrg_stride(int m) { return rgfft::rows(m) + ((8 - rgfft::rows(m) % 16) + 16) % 16; }
+
+// Register-staged forward x pass (FP32, nx = 2M, M a power of two; rgfft in
+// fft.cuh).  A CTA of L * M/16 threads owns L consecutive x-lines; thread
+// (line, t) forms the packed values z_e = x_{2e} + i x_{2e+1} of its first
+// FFT pass (e = t + q M/16) straight from the source -- f (FP64), f as pairs,
+// or the residual f - L p in pair arithmetic, two cells per 16-byte load --
+// the last pass leaves Z in shared memory and the untangle writes the nx/2 + 1
+// half spectrum.  Same cell arithmetic as k_xfwd.
+template <int SRC, int M, bool OPEN>
+__global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                                 const df* __restrict__ pdf, cpx<float>* spec,
+                                                 const cpx<float>* __restrict__ tw, int L) {
+  using T = float;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
+  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xrg_stride(M);
+  const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
+  const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
+  const uint32_t l0 = blockIdx.x * (uint32_t)L;
+  const uint32_t line = l0 + ll;
+  const bool valid = line < nlines;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // L lines of LS
+  cpx<T>* tws = buf + L * LS;                          // exp(-2 pi i t/nx), t < nx
+  for (int t = threadIdx.x; t < nx; t += blockDim.x) tws[t] = tw[t];
+  const uint32_t c0 = line * (uint32_t)nx;  // 32-bit offsets (grids up to 1024^3)
+  float vmax = 0.0f;
+  df fsum = {0.0f, 0.0f};
+  auto put = [&](int e, cpx<T> v) { buf[ll * LS + rgfft::row(e)] = v; };
+  if constexpr (SRC == SRC_F) {
+    const double2* fl = reinterpret_cast<const double2*>(in.f + c0);
+    float4* fo = fdf ? reinterpret_cast<float4*>(fdf + c0) : nullptr;
+    rgfft::run<T, false, M, 2, false>(
+        [&](int e) -> cpx<T> {
+          if (!valid) return {(T)0, (T)0};
+          const double2 x = __ldg(fl + e);
+          const df v0 = d2df(x.x), v1 = d2df(x.y);
+          if (fo) fo[e] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+          vmax = fmaxf(vmax, fmaxf(fabsf(v0.hi), fabsf(v1.hi)));
+          fsum = df_addz(df_addz(fsum, v0), v1);
+          return {df_to_f(v0), df_to_f(v1)};
+        },
+        put, buf + ll * LS, 1, t0, tws);
+  } else if constexpr (SRC == SRC_FDF) {
+    // f as pairs, written by the right-hand-side kernel (which also took ||f||)
+    const float4* fl = reinterpret_cast<const float4*>(fdf + c0);
+    rgfft::run<T, false, M, 2, false>(
+        [&](int e) -> cpx<T> {
+          if (!valid) return {(T)0, (T)0};
+          const float4 q = fl[e];
+          const df v0 = {q.x, q.y}, v1 = {q.z, q.w};
+          fsum = df_addz(df_addz(fsum, v0), v1);
+          return {df_to_f(v0), df_to_f(v1)};
+        },
+        put, buf + ll * LS, 1, t0, tws);
+  } else {
+    // residual r = f - L p in pairs, second differences as (p+ + p-) - 2 p
+    const df lcx = sc->K.lx, lcy = sc->K.ly, lcz = sc->K.lz;
+    const df fmean = sc->f_mean;  // left out of the residual (the solve drops it)
+    const uint32_t ny = (uint32_t)g.ny, nzu = (uint32_t)g.nz;
+    const uint32_t k = valid ? fdiv(line, g.fd_ny) : 0u, j = line - k * ny;
+    const uint32_t plane = ny * (uint32_t)nx;
+    const df* pl = pdf + c0;
+    const float4* pc4 = reinterpret_cast<const float4*>(pl);
+    const float4* pzm4 = reinterpret_cast<const float4*>(pdf + (k == 0 ? c0 + (nzu - 1) * plane : c0 - plane));
+    const float4* pzp4 = reinterpret_cast<const float4*>(pdf + (k + 1 == nzu ? c0 - (nzu - 1) * plane : c0 + plane));
+    const bool has_ym = j > 0, has_yp = j + 1 < ny;
+    const float4* pym4 = reinterpret_cast<const float4*>(pdf + (has_ym ? c0 - nx : c0));
+    const float4* pyp4 = reinterpret_cast<const float4*>(pdf + (has_yp ? c0 + nx : c0));
+    const float4* f4 = reinterpret_cast<const float4*>(fdf + c0);
+    auto res = [&](df pc, df pxm, df pxp, df pym, df pyp, df pzm, df pzp, df fv) {
+      const df p2 = df_ldexp2(pc);
+      const df lx = df_subz(df_addz(pxp, pxm), p2);
+      const df lz = df_subz(df_addz(pzp, pzm), p2);
+      const df ly = df_subz(df_addz(pyp, pym), p2);
+      const df lap = df_addz(df_addz(df_mulz(lx, lcx), df_mulz(ly, lcy)), df_mulz(lz, lcz));
+      return df_to_f(df_subz(df_subz(fv, fmean), lap));
+    };
+    rgfft::run<T, false, M, 2, false>(
+        [&](int e) -> cpx<T> {
+          if (!valid) return {(T)0, (T)0};
+          const int i0 = 2 * e;
+          const float4 c = pc4[e];
+          const df pxm = pl[i0 == 0 ? nx - 1 : i0 - 1];
+          const df pxp = pl[i0 + 2 == nx ? 0 : i0 + 2];
+          const float4 zm = pzm4[e], zp = pzp4[e];
+          const float4 ym = has_ym ? pym4[e] : c;  // wall mirror below the bottom cell
+          // above the top cell: the wall mirror, or the outflow ghost -p (p = 0 on the face)
+          const float4 yp = has_yp ? pyp4[e] : (OPEN ? make_float4(-c.x, -c.y, -c.z, -c.w) : c);
+          const float4 fv = f4[e];
+          const df a0 = {c.x, c.y}, a1 = {c.z, c.w};
+          const float r0 = res(a0, pxm, a1, df{ym.x, ym.y}, df{yp.x, yp.y}, df{zm.x, zm.y}, df{zp.x, zp.y},
+                               df{fv.x, fv.y});
+          const float r1 = res(a1, a0, pxp, df{ym.z, ym.w}, df{yp.z, yp.w}, df{zm.z, zm.w}, df{zp.z, zp.w},
+                               df{fv.z, fv.w});
+          vmax = fmaxf(vmax, fmaxf(fabsf(r0), fabsf(r1)));
+          return {r0, r1};
+        },
+        put, buf + ll * LS, 1, t0, tws);
+  }
+  if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
+  else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
+  if (SRC == SRC_F || SRC == SRC_FDF) {
+    // per-CTA sum of f, totalled in a fixed order by the next kernel (finish_sums)
+    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->x_parts = (int)gridDim.x;
+  }
+  __syncthreads();
+  // untangle: X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, W = exp(-2 pi i/nx)
+  for (int idx = threadIdx.x; idx < L * nxh; idx += blockDim.x) {
+    const int lq = idx / nxh, kx = idx - lq * nxh;
+    if (l0 + lq >= nlines) continue;
+    const cpx<T> zk = buf[lq * LS + rgfft::row(kx == M ? 0 : kx)];
+    const cpx<T> zc = buf[lq * LS + rgfft::row(kx == 0 ? 0 : M - kx)];
+    const cpx<T> a = {zk.x + zc.x, zk.y - zc.y};
+    const cpx<T> b = {zk.x - zc.x, zk.y + zc.y};
+    const cpx<T> wb = cmul(tws[kx], b);
+    cpx<T> X;
+    X.x = (T)0.5 * (a.x + wb.y);
+    X.y = (T)0.5 * (a.y - wb.x);
+    spec[(l0 + lq) * (uint32_t)nxh + kx] = X;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // z pass
 // ---------------------------------------------------------------------------
@@ -259,6 +385,35 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
     const int k = idx >> tl2, c = idx & (tkx - 1);
     if (kx0 + c < nxh) spec[base + k * rowstride + c] = r[idx];
   }
+}
+
+// Register-staged z pass (FP32, power-of-two nz; rgfft in fft.cuh): one CTA
+// per (j, tile of L kx columns), L * nz/16 threads; the first pass reads the
+// columns from the spectrum and the last pass writes them back, so each
+// element crosses shared memory once.
+template <typename T, bool INV, int N>
+__global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw, int L,
+                                                 const DevScalars* sc, DevScalars* fin) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (fin && blockIdx.x == 0) finish_sums(fin, g);  // uniform over the CTA
+  if (sc && sc->done) return;
+  const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
+  const uint32_t ntile = (nxh + L - 1) / L;
+  const uint32_t j = blockIdx.x / ntile;
+  const uint32_t kx0 = (blockIdx.x - j * ntile) * L;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/nz)
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
+  const int line = threadIdx.x & (L - 1), t0 = threadIdx.x >> ilog2_dev(L);
+  const bool valid = kx0 + line < nxh;
+  const uint32_t rs = (uint32_t)g.ny * nxh;  // kz stride (32-bit offsets: spectra below 2^32 elements)
+  cpx<T>* col = spec + (j * nxh + kx0 + line);
+  rgfft::run<T, INV, N, 1, false>(
+      [&](int e) { return valid ? col[(uint32_t)e * rs] : cpx<T>{(T)0, (T)0}; },
+      [&](int e, cpx<T> v) {
+        if (valid) col[(uint32_t)e * rs] = v;
+      },
+      buf + line, L, t0, tws);
 }
 
 // ---------------------------------------------------------------------------
@@ -437,6 +592,77 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
   }
 }
 
+// Register-staged form of k_ydct (FP32, power-of-two ny; rgfft in fft.cuh):
+// the reordered line is read straight from the spectrum by the first pass of
+// the DCT-II's FFT, the eigenvalue division works on the shared buffer, and
+// the last pass of the inverse writes the reordered result back.  Same
+// arithmetic as k_ydct.
+template <typename T, int N>
+__global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw,
+                                                 const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
+                                                 const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
+  const uint32_t ntile = (nxh + L - 1) / L;
+  const uint32_t kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * L;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/ny)
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
+  const int lg = ilog2_dev(L);
+  const int line = threadIdx.x & (L - 1), t0 = threadIdx.x >> lg;
+  const bool valid = kx0 + line < nxh;
+  cpx<T>* col = spec + (kz * (uint32_t)N * nxh + kx0 + line);
+  // v[p] = x_j with p = j/2 (even j) or N-1-(j-1)/2 (odd j)
+  auto jof = [](int p) { return p < N / 2 ? 2 * p : 2 * (N - 1 - p) + 1; };
+  rgfft::run<T, false, N, 1, false>(
+      [&](int p) { return valid ? col[(uint32_t)jof(p) * nxh] : cpx<T>{(T)0, (T)0}; },
+      [&](int e, cpx<T> v) { buf[rgfft::row(e) * L + line] = v; }, buf + line, L, t0, tws);
+  __syncthreads();
+  const T inv_n = (T)1 / (T)N;
+  const T lz = lam_z[kz];
+  constexpr int npair = N / 2 + 1;
+#pragma unroll 1
+  for (int idx = threadIdx.x; idx < npair * L; idx += blockDim.x) {
+    const int k = idx >> lg, c = idx & (L - 1);
+    const uint32_t kx = kx0 + c;
+    if (kx >= nxh) continue;
+    const T lxz = lam_x[kx] + lz;
+    cpx<T>* Vk = buf + rgfft::row(k) * L + c;
+    if (k == 0) {
+      const T lam = lxz + lam_y[0];
+      const cpx<T> v0 = *Vk;
+      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n / lam;  // zero mode pinned
+      *Vk = {v0.x * s, v0.y * s};
+      continue;
+    }
+    const int r = N - k;
+    cpx<T>* Vr = buf + rgfft::row(r) * L + c;
+    const cpx<T> vk = *Vk, vr = *Vr;
+    const cpx<T> wk = wq[k], wr = wq[r];
+    const cpx<T> wkc = {wk.x, -wk.y}, wrc = {wr.x, -wr.y};
+    const cpx<T> t1 = cmul(wk, vk), t2c = cmul(wkc, vr);
+    const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
+    const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
+    const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
+    const T sk = inv_n / (lxz + lam_y[k]), sr = inv_n / (lxz + lam_y[r]);
+    const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
+    // V'_k = conj(w_k)(P_k - i P_r), V'_r = conj(w_r)(P_r - i P_k);  -i z = (z.y, -z.x)
+    *Vk = cmul(wkc, cpx<T>{pk.x + pr.y, pk.y - pr.x});
+    if (r != k) *Vr = cmul(wrc, cpx<T>{pr.x + pk.y, pr.y - pk.x});
+  }
+  __syncthreads();
+  rgfft::run<T, true, N, 1, true>(
+      [&](int e) { return buf[rgfft::row(e) * L + line]; },
+      [&](int e, cpx<T> v) { buf[rgfft::row(e) * L + line] = v; }, buf + line, L, t0, tws);
+  __syncthreads();
+  // x_j = v'[p(j)]: copy-out row by row (j = idx / L), consecutive threads on consecutive columns
+  for (int idx = threadIdx.x; idx < N * L; idx += blockDim.x) {
+    const int jj = idx >> lg, c = idx & (L - 1);
+    const int pj = (jj & 1) ? N - 1 - (jj >> 1) : (jj >> 1);
+    if (kx0 + c < nxh) spec[kz * (uint32_t)N * nxh + (uint32_t)jj * nxh + kx0 + c] = buf[rgfft::row(pj) * L + c];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // inverse x pass
 // ---------------------------------------------------------------------------
@@ -502,9 +728,115 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
   }
 }
 
+// Register-staged inverse x pass (FP32, nx = 2M, M a power of two): thread
+// (line, t) forms the packed values Z_k of its first inverse-FFT pass from
+// X_k and X_{M-k} read straight from the spectrum, and the last pass stores
+// (or adds) the real pairs of cells 2n, 2n+1 with one 16-byte access.  Same
+// arithmetic as k_xinv.
+template <int MODE, int M>
+__global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
+                                                 double scale, const cpx<float>* __restrict__ tw, int L,
+                                                 const DevScalars* sc) {
+  using T = float;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (sc && sc->done) return;
+  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xrg_stride(M);
+  const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
+  const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
+  const uint32_t line = blockIdx.x * (uint32_t)L + ll;
+  const bool valid = line < nlines;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* tws = buf + L * LS;
+  for (int t = threadIdx.x; t < nx; t += blockDim.x) tws[t] = tw[t];
+  const cpx<T>* X = spec + line * (uint32_t)nxh;
+  const uint32_t c0 = line * (uint32_t)nx;
+  const df sdf = d2df(scale);
+  // Z_k = E_k + i O_k, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(W^k)/2
+  auto ld = [&](int k) -> cpx<T> {
+    if (!valid) return {(T)0, (T)0};
+    const cpx<T> xk = X[k];
+    const cpx<T> xc = X[M - k];
+    const cpx<T> e = {(T)0.5 * (xk.x + xc.x), (T)0.5 * (xk.y - xc.y)};
+    const cpx<T> dd = {(T)0.5 * (xk.x - xc.x), (T)0.5 * (xk.y + xc.y)};
+    cpx<T> w = tw[k];
+    w.y = -w.y;
+    const cpx<T> o = cmul(dd, w);
+    return {e.x - o.y, e.y + o.x};
+  };
+  auto st = [&](int n, cpx<T> v) {
+    if (!valid) return;
+    const uint32_t o = c0 + 2 * (uint32_t)n;
+    if (MODE == XI_F64) {
+      reinterpret_cast<double2*>(p)[o >> 1] = make_double2(scale * (double)v.x, scale * (double)v.y);
+    } else {
+      const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
+      float4* q4 = reinterpret_cast<float4*>(pdf) + (o >> 1);
+      if (MODE == XI_DF) {
+        *q4 = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+      } else {
+        const float4 q = *q4;
+        const df s0 = df_add(df{q.x, q.y}, d0), s1 = df_add(df{q.z, q.w}, d1);
+        *q4 = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+      }
+    }
+  };
+  if constexpr (MODE != XI_DF_ACC) {
+    rgfft::run<T, true, M, 2, false>(ld, st, buf + ll * LS, 1, t0, tws);
+  } else {
+    // p += s x: the last pass leaves x in shared memory; the update then runs
+    // over consecutive cell pairs with four read-modify-writes in flight
+    rgfft::run<T, true, M, 2, false>(ld, [&](int e, cpx<T> v) { buf[ll * LS + rgfft::row(e)] = v; },
+                                     buf + ll * LS, 1, t0, tws);
+    __syncthreads();
+    const uint32_t l0 = blockIdx.x * (uint32_t)L;
+    constexpr int U = 4;
+    for (int b0 = threadIdx.x; b0 < L * M; b0 += U * blockDim.x) {
+      float4 q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x;
+        const int lq = idx / M;
+        if (idx < L * M && l0 + lq < nlines)
+          q[u] = reinterpret_cast<const float4*>(pdf)[(l0 + lq) * (uint32_t)M + (idx - lq * M)];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * blockDim.x;
+        const int lq = idx / M, n = idx - lq * M;
+        if (idx >= L * M || l0 + lq >= nlines) continue;
+        const cpx<T> v = buf[lq * LS + rgfft::row(n)];
+        const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
+        const df s0 = df_add(df{q[u].x, q[u].y}, d0), s1 = df_add(df{q[u].z, q[u].w}, d1);
+        reinterpret_cast<float4*>(pdf)[(l0 + lq) * (uint32_t)M + n] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Lines per CTA of the register-staged passes: the tuned tile, raised so that a
+// CTA (L * N/16 threads) holds at least one full warp.
+template <int N>
+int rg_lines(int tile) {
+  return tile > 32 / (N / 16) ? tile : 32 / (N / 16);
+}
+template <typename T>
+size_t rg_smem(int n, int L) {
+  return sizeof(cpx<T>) * ((size_t)rgfft::rows(n) * L + (size_t)n);
+}
+// Lines per CTA of the register-staged x passes: the tuned x_lines, kept
+// within one warp .. 256 threads (M/16 threads per line).
+template <int M>
+int rg_xlines(int lpb) {
+  const int lo = 32 / (M / 16) > 1 ? 32 / (M / 16) : 1, hi = 256 / (M / 16);
+  return lpb < lo ? lo : (lpb > hi ? hi : lpb);
+}
+inline size_t xrg_smem(int nx, int L) {
+  return sizeof(cpx<float>) * ((size_t)xrg_stride(nx / 2) * L + (size_t)nx);
+}
+
 template <typename T>
 size_t xfwd_smem(int nx, int lpb) {
   return sizeof(cpx<T>) * (2 * (size_t)lpb * (nx / 2 + 1) + (size_t)nx);
@@ -555,6 +887,23 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
   return with_len<T>(g.nx / 2, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
+    if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+      if (do_fft) {
+        const int L = rg_xlines<N>(lpb);
+        const int gr = (nlines + L - 1) / L;
+        const size_t smr = xrg_smem(g.nx, L);
+        auto go = [&](auto kernel) -> cudaError_t {
+          cudaError_t e2 = allow_smem(kernel, smr);
+          if (e2 != cudaSuccess) return e2;
+          kernel<<<gr, L * (N / 16), smr, st>>>(g, in, sc, slot, fdf, pdf, (cpx<float>*)spec, (const cpx<float>*)tw, L);
+          return cudaGetLastError();
+        };
+        if (src == SRC_F) return go(k_xfwd_rg<SRC_F, N, false>);
+        if (src == SRC_FDF) return go(k_xfwd_rg<SRC_FDF, N, false>);
+        if (!g.top_open) return go(k_xfwd_rg<SRC_RESID, N, false>);
+        return go(k_xfwd_rg<SRC_RESID, N, true>);
+      }
+    }
     if (src == SRC_F) {
       if ((e = allow_smem(k_xfwd<T, SRC_F, true, N>, sm)) != cudaSuccess) return e;
       k_xfwd<T, SRC_F, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
@@ -578,6 +927,7 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
   });
 }
 
+
 template <typename T>
 cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw,
                         int tkx, const DevScalars* sc, DevScalars* fin, cudaStream_t st) {
@@ -587,6 +937,19 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
   return with_len<T>(g.nz, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
+    if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+      const int L = rg_lines<N>(tkx);
+      const int gr = g.ny * ((nxh + L - 1) / L);
+      const size_t smr = rg_smem<T>(N, L);
+      if (inverse) {
+        if ((e = allow_smem(k_zfft_rg<T, true, N>, smr)) != cudaSuccess) return e;
+        k_zfft_rg<T, true, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, L, sc, fin);
+      } else {
+        if ((e = allow_smem(k_zfft_rg<T, false, N>, smr)) != cudaSuccess) return e;
+        k_zfft_rg<T, false, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, L, sc, fin);
+      }
+      return cudaGetLastError();
+    }
     if (inverse) {
       if ((e = allow_smem(k_zfft<T, true, N>, sm)) != cudaSuccess) return e;
       k_zfft<T, true, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, tkx, sc, fin);
@@ -629,6 +992,15 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
   const size_t sm = zfft_smem<T>(g.ny, tky);
   return with_len<T>(g.ny, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
+    if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+      const int L = rg_lines<N>(tky);
+      const int gr = g.nz * ((nxh + L - 1) / L);
+      const size_t smr = rg_smem<T>(N, L);
+      cudaError_t e = allow_smem(k_ydct_rg<T, N>, smr);
+      if (e != cudaSuccess) return e;
+      k_ydct_rg<T, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, wq, lam_x, lam_y, lam_z, L);
+      return cudaGetLastError();
+    }
     cudaError_t e = allow_smem(k_ydct<T, N>, sm);
     if (e != cudaSuccess) return e;
     k_ydct<T, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky);
@@ -645,6 +1017,21 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   return with_len<T>(g.nx / 2, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
+    if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+      const int L = rg_xlines<N>(lpb);
+      const int gr = (nlines + L - 1) / L;
+      const size_t smr = xrg_smem(g.nx, L);
+      auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e2 = allow_smem(kernel, smr);
+        if (e2 != cudaSuccess) return e2;
+        kernel<<<gr, L * (N / 16), smr, st>>>(g, (const cpx<float>*)spec, p, pdf, scale, (const cpx<float>*)tw, L,
+                                               sc);
+        return cudaGetLastError();
+      };
+      if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N>);
+      if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N>);
+      return go(k_xinv_rg<XI_DF_ACC, N>);
+    }
     if (mode == XI_F64) {
       if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
       k_xinv<T, XI_F64, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);

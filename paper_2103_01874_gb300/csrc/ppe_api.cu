@@ -247,11 +247,12 @@ int choose_lpb(int nx) {
   return l;
 }
 
-// kx columns per CTA of the z and y passes: 8 (64-byte FP32 / 128-byte FP64
-// rows; measured best at 256^3 on a GB300), fewer when the tile would not fit
-int choose_tkx(int nz, bool fp32) {
+// kx columns per CTA of the z and y passes: 16 for the FP32 z pass (128-byte
+// rows), 8 otherwise (64-byte FP32 / 128-byte FP64 rows) -- measured best at
+// 256^3 on a GB300 -- fewer when the tile would not fit
+int choose_tkx(int nz, bool fp32, bool zpass) {
   const size_t cb = fp32 ? 8 : 16;
-  int t = 8;
+  int t = (fp32 && zpass) ? 16 : 8;
   while (t > 2 && cb * (2 * (size_t)t * nz + nz) > 160 * 1024) t /= 2;
   return t;
 }
@@ -726,8 +727,8 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->rp_half = radix_plan(g->nx / 2, maxr);
   P->rp_z = radix_plan(g->nz, maxr);
   P->lpb = choose_lpb(g->nx);
-  P->tkx = choose_tkx(g->nz, P->fp32);
-  P->tky = choose_tkx(g->ny, P->fp32);
+  P->tkx = choose_tkx(g->nz, P->fp32, true);
+  P->tky = choose_tkx(g->ny, P->fp32, false);
   P->rp_y = radix_plan(g->ny, maxr);
   P->cplx_bytes = P->fp32 ? 8 : 16;
 

@@ -67,9 +67,13 @@ __device__ __forceinline__ FaceOut face_q(df rl, df rh, df pl, df ph, df us, df 
   return o;
 }
 
+// p_hat = 2 p^n - p^{n-1} (Eq. (32)): one FP64 fused multiply-add (a single
+// rounding, on the FP64 pipe, which these kernels leave otherwise idle), then
+// one split into a pair
+__device__ __forceinline__ df phat_of(double pn, double pnm1) { return d2df(fma(2.0, pn, -pnm1)); }
+
 __device__ __forceinline__ df phat_df(const double* pn, const double* pnm1, size_t c) {
-  // p_hat = 2 p^n - p^{n-1}, Eq. (32)
-  return df_sub(df_ldexp2(d2df(__ldg(pn + c))), d2df(__ldg(pnm1 + c)));
+  return phat_of(__ldg(pn + c), __ldg(pnm1 + c));
 }
 
 struct Nbr {
@@ -134,10 +138,24 @@ __device__ __forceinline__ void sum_parts_fixed(const double2* part, int n, doub
   __shared__ double red_p[2][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double x = 0.0, y = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double2 v = __ldcg(part + i);
-    x += v.x;
-    y += v.y;
+  // each thread adds its entries i = threadIdx.x + m blockDim.x in order of m;
+  // eight loads are issued before their additions (the order is unchanged)
+  constexpr int U = 8;
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+    double2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < n ? __ldcg(part + i) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n) {
+        x += v[u].x;
+        y += v[u].y;
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     x += __shfl_down_sync(0xffffffffu, x, o);

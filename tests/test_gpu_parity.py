@@ -171,11 +171,13 @@ from _gpu_util import dev_fields, project_gpu, to_dev  # noqa: E402
 
 
 @pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
-def test_tuning_does_not_change_results(precision):
+@pytest.mark.parametrize("grid", [(48, 24, 36), (64, 32, 64)])
+def test_tuning_does_not_change_results(precision, grid):
     """Launch shapes (tile sizes, marching chunk) change no bit of the outputs,
-    including ragged last tiles; invalid shapes are rejected."""
+    including ragged last tiles; invalid shapes are rejected.  The power-of-two
+    grid takes the register-staged FP32 transforms in x, y and z."""
     import torch
-    fl = fields.make_fields(48, 24, 36, seed=17, recipe="multimode", width=4.0)
+    fl = fields.make_fields(*grid, seed=17, recipe="multimode", width=4.0)
     d = dev_fields(fl)
     shapes = [dict(rhs_lines=4, rhs_planes=16, x_lines=32, z_cols=8, y_cols=16),
               dict(rhs_lines=1, rhs_planes=5, x_lines=1, z_cols=1, y_cols=1),
