@@ -888,7 +888,8 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
     if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
-      if (do_fft) {
+      // (the register-staged form reads f with 16-byte loads)
+      if (do_fft && (src != SRC_F || ((uintptr_t)in.f & 15u) == 0)) {
         const int L = rg_xlines<N>(lpb);
         const int gr = (nlines + L - 1) / L;
         const size_t smr = xrg_smem(g.nx, L);
@@ -1017,7 +1018,9 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   return with_len<T>(g.nx / 2, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
+    // (the register-staged form writes an FP64 p with 16-byte stores)
     if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+      if (mode != XI_F64 || ((uintptr_t)p & 15u) == 0) {
       const int L = rg_xlines<N>(lpb);
       const int gr = (nlines + L - 1) / L;
       const size_t smr = xrg_smem(g.nx, L);
@@ -1031,6 +1034,7 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
       if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N>);
       if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N>);
       return go(k_xinv_rg<XI_DF_ACC, N>);
+      }
     }
     if (mode == XI_F64) {
       if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
