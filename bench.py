@@ -524,6 +524,8 @@ def run_served(args, dev):
     for r in warm:
         r.rid = -1 - r.rid
     srv.run(warm)
+    # and a resident pool of at least 3 plans per size class and precision
+    srv.reserve([(s, p) for s in shapes for p in (ppe.FP64, ppe.FP32_REFINE)], per_class=3)
     created_warm = srv.plans_created
     stats, _ = srv.run(reqs)
     srv.close()

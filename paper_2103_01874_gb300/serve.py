@@ -107,6 +107,26 @@ class Server:
             return plan, 0
         return None, self.ex.plan_bytes_for(req.shape, req.precision)
 
+    def reserve(self, classes, per_class: int = 2) -> int:
+        """Create idle plans ahead of traffic, so that each (shape, precision)
+        class holds at least `per_class` resident plans and no request waits
+        for a plan to be built (allocation and graph capture take tens of ms
+        for the large grids).  Stops at the memory budget; returns the number
+        of plans created."""
+        made = 0
+        for shape, precision in classes:
+            key = (shape, precision)
+            while len(self.idle.get(key, [])) < per_class:
+                need = self.ex.plan_bytes_for(shape, precision)
+                if self._in_use() + need > self.budget:
+                    return made
+                plan = self.ex.create_plan(shape, precision)
+                self.plans_created += 1
+                self.plan_bytes += need
+                self.idle.setdefault(key, []).append(plan)
+                made += 1
+        return made
+
     def _return_plan(self, req, plan):
         key = (req.shape, req.precision)
         self.idle.setdefault(key, []).append(plan)

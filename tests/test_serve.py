@@ -85,3 +85,20 @@ def test_oversized_request_is_rejected_not_blocking():
     reqs.insert(5, serve.Request(999, (512, 512, 512), 1, 0, reqs[4].arrival))
     srv, ex, st, _ = _run(reqs, budget=50_000_000)
     assert st.rejected == 1 and st.completed == 20
+
+
+def test_reserve_builds_a_resident_pool_within_budget():
+    clk = VClock()
+    ex = serve.FakeExecutor(lambda r: 0.002, clk)
+    classes = [(s, p) for s in SHAPES for p in (0, 1)]
+    srv = Watch(ex, 10 ** 12, slots=4)
+    assert srv.reserve(classes, per_class=2) == 2 * len(classes)
+    assert srv.reserve(classes, per_class=2) == 0          # already resident
+    reqs = serve.poisson_requests(100, rate=2000.0, shapes=SHAPES, seed=3)
+    before = srv.plans_created
+    st, _ = srv.run(reqs, clock=clk, sleep=clk.sleep)
+    assert st.completed == 100
+    assert srv.plans_created - before <= 2 * len(classes)  # the pool absorbs most of the traffic
+    # a tight budget stops the reservation
+    tight = Watch(serve.FakeExecutor(lambda r: 0.002, VClock()), ex.plan_bytes_for(SHAPES[0], 0) + 1, slots=4)
+    assert tight.reserve(classes, per_class=2) == 1
