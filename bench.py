@@ -382,9 +382,41 @@ def run_gpu(args):
         res["served"] = run_served(args, dev)
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
+        res["precision"] = precision_report(fl, d, dev, stream)
     if dist is not None:
         dist.destroy_process_group()
     return res
+
+
+def precision_report(fl, d, dev, stream):
+    """Error of the FP32 solve + pair refinement against the FP64 oracle on the
+    bench workload, per refinement sweep: the projection with exactly k sweeps
+    (max_sweeps = k, no tolerance; k = 0 is the FP32 solve and the correction
+    alone), max |x - x_oracle| / max |x_oracle| for p, u, v, w, and the
+    relative residual the refinement test sees.  Part of the CPU-baseline leg
+    (the oracle runs once here, about 2 s on one core)."""
+    import torch
+    from oracle import ppe_oracle as O
+    from paper_2103_01874_gb300 import ppe
+    ref = O.project_fields(fl)
+    c = fl.shape
+    rows = []
+    for k in range(4):
+        o = dict(p=torch.empty(c, dtype=torch.float64, device=dev), u=torch.empty_like(d["u"]),
+                 v=torch.empty_like(d["v"]), w=torch.empty_like(d["w"]))
+        with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, refine_tol=0.0,
+                      max_sweeps=k, stream=stream) as plan:
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt,
+                         o["p"], o["u"], o["v"], o["w"])
+            info = plan.info(allow_not_converged=True)
+        row = {"sweeps": int(info.sweeps), "rel_residual": float(info.rel_residual)}
+        for key in ("p", "u", "v", "w"):
+            g = o[key].cpu().numpy()
+            row[f"err_{key}"] = float(abs(g - ref[key]).max() / abs(ref[key]).max())
+        rows.append(row)
+    return {"what": "FP32 solve + k pair-refinement sweeps (no tolerance) vs the FP64 oracle, 256^3 bench "
+                    "workload: max-norm error of p, u, v, w relative to the oracle's max, and the relative "
+                    "residual of the refinement test", "rows": rows}
 
 
 # ---------------------------------------------------------------------------
