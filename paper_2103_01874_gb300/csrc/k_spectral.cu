@@ -631,7 +631,9 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
     if (k == 0) {
       const T lam = lxz + lam_y[0];
       const cpx<T> v0 = *Vk;
-      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n / lam;  // zero mode pinned
+      // inv_n / lam as inv_n * (1/lam): inv_n is a power of two, so the correctly
+      // rounded reciprocal times it is the correctly rounded quotient
+      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n * __frcp_rn(lam);  // zero mode pinned
       *Vk = {v0.x * s, v0.y * s};
       continue;
     }
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
     const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
     const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
     const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
-    const T sk = inv_n / (lxz + lam_y[k]), sr = inv_n / (lxz + lam_y[r]);
+    const T sk = inv_n * __frcp_rn(lxz + lam_y[k]), sr = inv_n * __frcp_rn(lxz + lam_y[r]);
     const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
     // V'_k = conj(w_k)(P_k - i P_r), V'_r = conj(w_r)(P_r - i P_k);  -i z = (z.y, -z.x)
     *Vk = cmul(wkc, cpx<T>{pk.x + pr.y, pk.y - pr.x});
