@@ -183,6 +183,30 @@ ppe_status ppe_project(ppe_plan_t plan, const ppe_fields* fields);
  * ppe_get_info does. */
 ppe_status ppe_project_host(ppe_plan_t plan, const ppe_fields* host_fields);
 
+/* Pipelined form of ppe_project_host for a sequence of projections with host
+ * buffers: enqueues the input copies, the projection and the output copies
+ * and returns without waiting.  The plan keeps two sets of device staging
+ * buffers used in turn, with the input copies on one stream, the projection
+ * on the plan's stream and the output copies on a third, so that one call's
+ * input copies run while the previous call computes and its outputs travel
+ * back.  A call whose staging set is still in use first waits for the call
+ * that used it (two calls in flight at most).  The host buffers of a call
+ * (pinned memory, for the copies to be asynchronous) must stay untouched and
+ * its outputs unread until ppe_host_wait returns.  Returns PPE_ERR_INVALID_ARG
+ * on missing arguments or while the plan's stream is capturing, a CUDA or
+ * allocation error if enqueueing fails, else PPE_OK; the device-side status of
+ * the projections is reported by ppe_host_wait.  Staging: 9 arrays of the grid
+ * per set, allocated on first use.  No counterpart in the paper: it is the
+ * host-memory interface of the projection step. */
+ppe_status ppe_project_host_async(ppe_plan_t plan, const ppe_fields* host_fields);
+
+/* Waits for every ppe_project_host_async call of the plan and returns the
+ * first status other than PPE_OK among the calls retired since the previous
+ * ppe_host_wait (PPE_ERR_NOT_CONVERGED or PPE_ERR_INCOMPATIBLE_RHS as
+ * ppe_get_info reports it for that call; a CUDA error if a wait fails), else
+ * PPE_OK.  ppe_get_info afterwards describes the last projection. */
+ppe_status ppe_host_wait(ppe_plan_t plan);
+
 /* Eq. (31): the divergence constraint S = div u^{n+1} from the phase-wise
  * quantities (all device arrays of nx*ny*nz cells, cell layout):
  *   S = -(1 - C) comp_g - C comp_l + mdot (1/rho_g - 1/rho_l)

@@ -56,6 +56,16 @@ struct ppe_plan_s {
   cudaGraphExec_t pcg_exec;
   // ppe_project_host staging (allocated on first use)
   double* io[12];
+  // ppe_project_host_async: two staging sets used in turn, copy-in and
+  // copy-out streams, per-set events, the scalars of each set's projection
+  // (pinned host memory), and what the pipeline has retired so far
+  double* aio[2][9];
+  cudaStream_t acin, acout;
+  cudaEvent_t aev_in[2], aev_done[2], aev_out[2];
+  DevScalars* ahsc;   // [2], pinned
+  int aset;           // set of the next call
+  int abusy[2];       // set holds a call not yet retired
+  ppe_status astatus; // first non-OK status of the calls retired since the last ppe_host_wait
   size_t workspace;
   // per-kernel CUDA-event records (ppe_profile)
   int prof_on;
@@ -806,6 +816,20 @@ void ppe_destroy(ppe_plan_t P) {
   if (P->refine_exec) cudaGraphExecDestroy(P->refine_exec);
   if (P->project_exec) cudaGraphExecDestroy(P->project_exec);
   for (int i = 0; i < 12; ++i) cudaFree(P->io[i]);
+  if (P->acin) {
+    cudaStreamSynchronize(P->acin);
+    cudaStreamSynchronize(P->acout);
+  }
+  cudaStreamSynchronize(P->stream);
+  for (int b = 0; b < 2; ++b) {
+    for (int i = 0; i < 9; ++i) cudaFree(P->aio[b][i]);
+    if (P->aev_in[b]) cudaEventDestroy(P->aev_in[b]);
+    if (P->aev_done[b]) cudaEventDestroy(P->aev_done[b]);
+    if (P->aev_out[b]) cudaEventDestroy(P->aev_out[b]);
+  }
+  if (P->acin) cudaStreamDestroy(P->acin);
+  if (P->acout) cudaStreamDestroy(P->acout);
+  if (P->ahsc) cudaFreeHost(P->ahsc);
   if (P->prof_ev)
     for (cudaEvent_t e : *P->prof_ev) cudaEventDestroy(e);
   delete P->prof_ev;
@@ -1168,11 +1192,9 @@ ppe_status ppe_project_host(ppe_plan_t P, const ppe_fields* H) {
   return ppe_get_info(P, &info);  // synchronises; device-side status (convergence, compatibility)
 }
 
-ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
-  if (!P || !info) return PPE_ERR_INVALID_ARG;
-  DevScalars h;
-  PPE_TRY(cudaMemcpyAsync(&h, P->sc, sizeof(h), cudaMemcpyDeviceToHost, P->stream));
-  PPE_TRY(cudaStreamSynchronize(P->stream));
+namespace {
+// The report and status of one projection from a host copy of its scalars.
+ppe_status info_from(ppe_plan_t P, const DevScalars& h, ppe_info* info) {
   const double fmax = h.fmax_bits ? __builtin_bit_cast(double, h.fmax_bits) : 0.0;
   info->f_max = fmax;
   info->rho0 = __builtin_bit_cast(double, h.rho0_bits);
@@ -1206,6 +1228,105 @@ ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
     info->rel_residual = -1.0;
   }
   return incompatible ? PPE_ERR_INCOMPATIBLE_RHS : PPE_OK;
+}
+}  // namespace
+
+namespace {
+// Retire the call that used staging set b: wait for its output copies and fold
+// its status into the pipeline's.
+ppe_status async_retire(ppe_plan_t P, int b) {
+  if (!P->abusy[b]) return PPE_OK;
+  PPE_TRY(cudaEventSynchronize(P->aev_out[b]));
+  P->abusy[b] = 0;
+  ppe_info info;
+  const ppe_status st = info_from(P, P->ahsc[b], &info);
+  if (P->astatus == PPE_OK) P->astatus = st;
+  return PPE_OK;
+}
+}  // namespace
+
+ppe_status ppe_project_host_async(ppe_plan_t P, const ppe_fields* H) {
+  if (!P || !H || !H->u || !H->v || !H->w || !H->S || !H->rho || !H->p_n || !H->p_nm1 || !H->p || !H->u_out ||
+      !H->v_out || !H->w_out || !(H->dt > 0))
+    return PPE_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cst;
+  if (cudaStreamIsCapturing(P->stream, &cst) != cudaSuccess || cst != cudaStreamCaptureStatusNone)
+    return PPE_ERR_INVALID_ARG;
+  const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
+  const size_t nv = (size_t)P->g.nx * (P->g.ny + 1) * P->g.nz;
+  const size_t sizes[9] = {n, nv, n, n, n, n, n, n, n};  // u v w S rho p_n p_nm1 p f
+  if (!P->acin) {
+    PPE_TRY(cudaStreamCreateWithFlags(&P->acin, cudaStreamNonBlocking));
+    PPE_TRY(cudaStreamCreateWithFlags(&P->acout, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      PPE_TRY(cudaEventCreateWithFlags(&P->aev_in[b], cudaEventDisableTiming));
+      PPE_TRY(cudaEventCreateWithFlags(&P->aev_done[b], cudaEventDisableTiming));
+      PPE_TRY(cudaEventCreateWithFlags(&P->aev_out[b], cudaEventDisableTiming));
+    }
+    ppe_status s = alloc_status(cudaMallocHost((void**)&P->ahsc, 2 * sizeof(DevScalars)));
+    if (s != PPE_OK) return s;
+  }
+  const int b = P->aset;
+  ppe_status s = async_retire(P, b);  // the set's previous call must have left it
+  if (s != PPE_OK) return s;
+  const int nbuf = H->f ? 9 : 8;
+  for (int i = 0; i < nbuf; ++i)
+    if (!P->aio[b][i]) {
+      s = alloc_status(cudaMalloc((void**)&P->aio[b][i], sizes[i] * sizeof(double)));
+      if (s != PPE_OK) return s;
+    }
+  double** io = P->aio[b];
+  // inputs on the copy-in stream (after the set's previous outputs left)
+  PPE_TRY(cudaStreamWaitEvent(P->acin, P->aev_out[b], 0));
+  const double* src[7] = {H->u, H->v, H->w, H->S, H->rho, H->p_n, H->p_nm1};
+  for (int i = 0; i < 7; ++i)
+    PPE_TRY(cudaMemcpyAsync(io[i], src[i], sizes[i] * sizeof(double), cudaMemcpyHostToDevice, P->acin));
+  PPE_TRY(cudaEventRecord(P->aev_in[b], P->acin));
+  // the projection on the plan's stream, then its scalars to the host
+  PPE_TRY(cudaStreamWaitEvent(P->stream, P->aev_in[b], 0));
+  ppe_fields D;
+  D.u = io[0]; D.v = io[1]; D.w = io[2]; D.S = io[3]; D.rho = io[4];
+  D.p_n = io[5]; D.p_nm1 = io[6];
+  D.rho0 = H->rho0;
+  D.dt = H->dt;
+  D.p = io[7];
+  D.u_out = io[0]; D.v_out = io[1]; D.w_out = io[2];  // in place
+  D.f = H->f ? io[8] : nullptr;
+  s = ppe_project(P, &D);
+  if (s != PPE_OK) return s;
+  PPE_TRY(cudaMemcpyAsync(&P->ahsc[b], P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->stream));
+  PPE_TRY(cudaEventRecord(P->aev_done[b], P->stream));
+  // outputs on the copy-out stream
+  PPE_TRY(cudaStreamWaitEvent(P->acout, P->aev_done[b], 0));
+  PPE_TRY(cudaMemcpyAsync(H->p, D.p, n * sizeof(double), cudaMemcpyDeviceToHost, P->acout));
+  PPE_TRY(cudaMemcpyAsync(H->u_out, D.u_out, n * sizeof(double), cudaMemcpyDeviceToHost, P->acout));
+  PPE_TRY(cudaMemcpyAsync(H->v_out, D.v_out, nv * sizeof(double), cudaMemcpyDeviceToHost, P->acout));
+  PPE_TRY(cudaMemcpyAsync(H->w_out, D.w_out, n * sizeof(double), cudaMemcpyDeviceToHost, P->acout));
+  if (H->f) PPE_TRY(cudaMemcpyAsync(H->f, D.f, n * sizeof(double), cudaMemcpyDeviceToHost, P->acout));
+  PPE_TRY(cudaEventRecord(P->aev_out[b], P->acout));
+  P->abusy[b] = 1;
+  P->aset = b ^ 1;
+  return PPE_OK;
+}
+
+ppe_status ppe_host_wait(ppe_plan_t P) {
+  if (!P) return PPE_ERR_INVALID_ARG;
+  // oldest call first: the set after the next one to be used
+  for (int q = 0; q < 2; ++q) {
+    const ppe_status s = async_retire(P, P->aset ^ q);
+    if (s != PPE_OK) return s;
+  }
+  const ppe_status st = P->astatus;
+  P->astatus = PPE_OK;
+  return st;
+}
+
+ppe_status ppe_get_info(ppe_plan_t P, ppe_info* info) {
+  if (!P || !info) return PPE_ERR_INVALID_ARG;
+  DevScalars h;
+  PPE_TRY(cudaMemcpyAsync(&h, P->sc, sizeof(h), cudaMemcpyDeviceToHost, P->stream));
+  PPE_TRY(cudaStreamSynchronize(P->stream));
+  return info_from(P, h, info);
 }
 
 }  // extern "C"

@@ -80,6 +80,8 @@ SIGNATURES = {
     "ppe_correct": (c_int, [c_void_p] + [c_void_p] * 7 + [c_double, c_double] + [c_void_p] * 3),
     "ppe_project": (c_int, [c_void_p, POINTER(FieldsC)]),
     "ppe_project_host": (c_int, [c_void_p, POINTER(FieldsC)]),
+    "ppe_project_host_async": (c_int, [c_void_p, POINTER(FieldsC)]),
+    "ppe_host_wait": (c_int, [c_void_p]),
     "ppe_get_info": (c_int, [c_void_p, POINTER(Info)]),
     "ppe_destroy": (None, [c_void_p]),
     "ppe_strerror": (ctypes.c_char_p, [c_int]),
@@ -299,6 +301,20 @@ class Plan:
     def project_host(self, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
         fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
         _check(lib().ppe_project_host(self._h, ctypes.byref(fc)), "ppe_project_host")
+
+    def project_host_async(self, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f=None, rho0=-1.0):
+        """Enqueue a projection from host buffers (ppe_project_host_async); the
+        buffers must stay untouched until host_wait()."""
+        fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
+        _check(lib().ppe_project_host_async(self._h, ctypes.byref(fc)), "ppe_project_host_async")
+
+    def host_wait(self, allow_not_converged=False, allow_incompatible=False):
+        """Wait for the enqueued host projections (ppe_host_wait)."""
+        code = lib().ppe_host_wait(self._h)
+        if (code == 5 and allow_not_converged) or (code == 3 and allow_incompatible):
+            return code
+        _check(code, "ppe_host_wait")
+        return code
 
     def project_unsplit(self, u, v, w, S, rho, dt, p, u_out, v_out, w_out, tol=1e-10, max_iter=500):
         """The unsplit projection, Eqs. (29)-(30), by FFT-preconditioned CG (ppe_project_unsplit)."""
