@@ -665,6 +665,98 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
   }
 }
 
+// 256-point form of k_ydct_rg (radices 16 x 16) with the eigenvalue divide in
+// registers between the transforms.  After the second forward pass thread t
+// holds X_k for k = t + 16 q, which is the set the first inverse pass reads,
+// so only the partners X_{N-k} (held by thread 16 - t) cross shared memory.
+// Each thread forms V'_k for its own k with the operations k_ydct_rg uses for
+// that member of the pair (k, N-k) (the compiler may contract products into
+// sums differently, so the last bits can differ; the FP32 solve is refined).
+__global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
+                                                  const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
+                                                  const float* __restrict__ lam_y, const float* __restrict__ lam_z,
+                                                  int L) {
+  using T = float;
+  constexpr int N = 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
+  const uint32_t ntile = (nxh + L - 1) / L;
+  const uint32_t kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * L;
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/ny)
+  for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
+  const int lg = ilog2_dev(L);
+  const int line = threadIdx.x & (L - 1), t0 = threadIdx.x >> lg;  // t0 in [0, 16)
+  const uint32_t kx = kx0 + line;
+  const bool valid = kx < nxh;
+  cpx<T>* col = spec + (kz * (uint32_t)N * nxh + kx);
+  cpx<T>* ln = buf + line;
+  // v[p] = x_j with p = j/2 (even j) or N-1-(j-1)/2 (odd j)
+  auto jof = [](int p) { return p < N / 2 ? 2 * p : 2 * (N - 1 - p) + 1; };
+  cpx<T> v[16];
+  // forward pass 0 (the DCT-II's reordered line straight from the spectrum)
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = valid ? col[(uint32_t)jof(t0 + 16 * q) * nxh] : cpx<T>{(T)0, (T)0};
+  SmallDft<T, false, 16>::run(v);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) ln[rgfft::row(16 * t0 + q) * L] = v[q];
+  __syncthreads();
+  // forward pass 1: v[q] = X_{t0 + 16 q}
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = ln[rgfft::row(t0 + 16 * q) * L];
+#pragma unroll
+  for (int q = 1; q < 16; ++q) v[q] = cmul(v[q], tws[q * t0]);
+  SmallDft<T, false, 16>::run(v);
+  __syncthreads();  // every read of pass 1 before the exchange writes
+#pragma unroll
+  for (int q = 0; q < 16; ++q) ln[rgfft::row(t0 + 16 * q) * L] = v[q];
+  __syncthreads();
+  // divide by the eigenvalues (zero mode pinned); V'_k = conj(w_k)(P_k - i P_r)
+  const T inv_n = (T)1 / (T)N;
+  const T lxz = (valid ? lam_x[kx] : (T)0) + lam_z[kz];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = t0 + 16 * q;
+    if (k == 0) {
+      // inv_n / lam as inv_n * (1/lam): inv_n is a power of two
+      const T s0 = (kx == 0 && kz == 0) ? (T)0 : inv_n * __frcp_rn(lxz + lam_y[0]);
+      v[0] = {v[0].x * s0, v[0].y * s0};
+      continue;
+    }
+    const int r = N - k;
+    const cpx<T> vk = v[q], vr = ln[rgfft::row(r) * L];
+    const cpx<T> wk = wq[k], wr = wq[r];
+    const cpx<T> wkc = {wk.x, -wk.y}, wrc = {wr.x, -wr.y};
+    const cpx<T> t1 = cmul(wk, vk), t2c = cmul(wkc, vr);
+    const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
+    const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
+    const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
+    const T sk = inv_n * __frcp_rn(lxz + lam_y[k]), sr = inv_n * __frcp_rn(lxz + lam_y[r]);
+    const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
+    v[q] = cmul(wkc, cpx<T>{pk.x + pr.y, pk.y - pr.x});
+  }
+  __syncthreads();  // the partners' reads before the inverse overwrites the buffer
+  // inverse pass 0 from registers
+  SmallDft<T, true, 16>::run(v);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) ln[rgfft::row(16 * t0 + q) * L] = v[q];
+  __syncthreads();
+  // inverse pass 1: outputs t0 + 16 q, back to the spectrum in physical order
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = ln[rgfft::row(t0 + 16 * q) * L];
+#pragma unroll
+  for (int q = 1; q < 16; ++q) {
+    cpx<T> w = tws[q * t0];
+    w.y = -w.y;
+    v[q] = cmul(v[q], w);
+  }
+  SmallDft<T, true, 16>::run(v);
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) col[(uint32_t)jof(t0 + 16 * q) * nxh] = v[q];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // inverse x pass
 // ---------------------------------------------------------------------------
@@ -999,6 +1091,14 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
       const int L = rg_lines<N>(tky);
       const int gr = g.nz * ((nxh + L - 1) / L);
       const size_t smr = rg_smem<T>(N, L);
+      if constexpr (N == 256) {
+        cudaError_t e = allow_smem(k_ydct256, smr);
+        if (e != cudaSuccess) return e;
+        k_ydct256<<<gr, L * (N / 16), smr, st>>>(g, (cpx<float>*)spec, (const cpx<float>*)tw,
+                                                 (const cpx<float>*)wq, (const float*)lam_x, (const float*)lam_y,
+                                                 (const float*)lam_z, L);
+        return cudaGetLastError();
+      }
       cudaError_t e = allow_smem(k_ydct_rg<T, N>, smr);
       if (e != cudaSuccess) return e;
       k_ydct_rg<T, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, wq, lam_x, lam_y, lam_z, L);
