@@ -430,92 +430,97 @@ __global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const 
 // bit for bit for J <= j <= N-2.  For kx = kz = 0 the matrix is singular (the
 // constant mode): m_0 = 0 pins x_0 = 0, the mean of d is removed first and the
 // mean of x afterwards, which gives the zero-mean solution.
-// One CTA per tile of `tl` consecutive kx lines at one kz: the tile (all j) is
-// copied to shared memory with asynchronous copies, the tl multiplier tables are
-// gathered into shared memory, one thread per line runs both sweeps in shared
-// memory, and the tile is written back.
+// One thread per (kx, kz) line, walking the line in global memory: in the
+// spectrum layout [kz][j][kx] the threads of a warp (consecutive kx) read and
+// write 32 consecutive elements per j, and each sweep moves in chunks of 8
+// elements whose loads (and multipliers) are issued before the chunk's
+// recurrence runs.  Nothing is staged in shared memory, so every line of the
+// spectrum has its thread resident at once (the shared-memory tile allowed
+// about 16 lines per CTA).  Same arithmetic, in the same order, as the
+// recurrences above.
 template <typename T>
 __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const T* __restrict__ tab,
                                                  const int* __restrict__ line_off, const int* __restrict__ line_len,
-                                                 T a, int tl, const DevScalars* sc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                 T a, const DevScalars* sc) {
   if (sc && sc->done) return;
   const int nxh = g.nx / 2 + 1, ny = g.ny;
-  const int ntile = (nxh + tl - 1) / tl;
-  const int kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * tl;
-  cpx<T>* d = reinterpret_cast<cpx<T>*>(smem_raw);      // [ny][tl]
-  T* tm = reinterpret_cast<T*>(d + (size_t)ny * tl);     // [tl][ny + 1]
-  const size_t base = (size_t)kz * ny * nxh + kx0;
-  const int tl2 = ilog2_dev(tl);
-  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
-    const int j = idx >> tl2, c = idx & (tl - 1);
-    if (kx0 + c < nxh)
-      cp_async<sizeof(cpx<T>)>(&d[idx], &spec[base + (size_t)j * nxh + c]);
-    else
-      d[idx] = {(T)0, (T)0};
-  }
-  // multipliers m_j of each line: stored entries, then m_inf, and m_last at j = ny-1
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
-    const int c = (int)fdiv(idx, g.fd_ny), j = idx - c * ny;
-    T m = (T)0;
-    if (kx0 + c < nxh) {
-      const int line = kz * nxh + kx0 + c;
-      const int off = line_off[line], J = line_len[line];
-      m = (j < J) ? tab[off + 2 + j] : ((j < ny - 1) ? tab[off] : tab[off + 1]);
+  const int kz = blockIdx.y;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kx >= nxh) return;  // no barriers below
+  const int line = kz * nxh + kx;
+  const int off = line_off[line], J = line_len[line];
+  const T m_inf = tab[off], m_last = tab[off + 1];
+  const size_t stride = (size_t)nxh;
+  cpx<T>* col = spec + (size_t)kz * ny * nxh + kx;
+  auto mult = [&](int jj) { return jj < J ? tab[off + 2 + jj] : (jj < ny - 1 ? m_inf : m_last); };
+  const bool zero_line = !g.top_open && kz == 0 && kx == 0;  // the wall problem's singular line
+  cpx<T> shift = {(T)0, (T)0};
+  if (zero_line) {
+    double sx = 0.0, sy = 0.0;
+    for (int jj = 0; jj < ny; ++jj) {
+      sx += (double)col[jj * stride].x;
+      sy += (double)col[jj * stride].y;
     }
-    tm[c * (ny + 1) + j] = m;
+    shift.x = (T)(sx / ny);
+    shift.y = (T)(sy / ny);
   }
-  cp_async_wait_all();
-  __syncthreads();
-  const int c = threadIdx.x;
-  if (c < tl && kx0 + c < nxh) {
-    const T* m = tm + c * (ny + 1);
-    const bool zero_line = !g.top_open && kz == 0 && kx0 + c == 0;  // the wall problem's singular line
-    cpx<T> shift = {(T)0, (T)0};
-    if (zero_line) {
-      double sx = 0.0, sy = 0.0;
-      for (int j = 0; j < ny; ++j) {
-        sx += (double)d[j * tl + c].x;
-        sy += (double)d[j * tl + c].y;
+  constexpr int C = 8;
+  cpx<T> prev = {(T)0, (T)0};
+  for (int j0 = 0; j0 < ny; j0 += C) {  // the last chunk may be short (ny = 2^a 3^b)
+    cpx<T> d[C];
+    T m[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      if (j0 + u < ny) {
+        d[u] = col[(j0 + u) * stride];
+        m[u] = mult(j0 + u);
       }
-      shift.x = (T)(sx / ny);
-      shift.y = (T)(sy / ny);
     }
-    cpx<T> prev = {(T)0, (T)0};
-    for (int j = 0; j < ny; ++j) {
-      const T mj = m[j];
-      cpx<T> v = d[j * tl + c];
-      v.x = (v.x - shift.x - a * prev.x) * mj;
-      v.y = (v.y - shift.y - a * prev.y) * mj;
-      d[j * tl + c] = v;
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      if (j0 + u >= ny) break;
+      cpx<T> v = d[u];
+      v.x = (v.x - shift.x - a * prev.x) * m[u];
+      v.y = (v.y - shift.y - a * prev.y) * m[u];
+      col[(j0 + u) * stride] = v;
       prev = v;
     }
-    for (int j = ny - 2; j >= 0; --j) {
-      const T cj = a * m[j];
-      cpx<T> v = d[j * tl + c];
+  }
+  // backward: j = ny-2 .. 0 in chunks of 8 from the top
+  for (int j1 = ny - 2; j1 >= 0; j1 -= C) {
+    cpx<T> d[C];
+    T m[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      const int jj = j1 - u;
+      if (jj >= 0) {
+        d[u] = col[jj * stride];
+        m[u] = mult(jj);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      const int jj = j1 - u;
+      if (jj < 0) break;
+      const T cj = a * m[u];
+      cpx<T> v = d[u];
       v.x -= cj * prev.x;
       v.y -= cj * prev.y;
-      d[j * tl + c] = v;
+      col[jj * stride] = v;
       prev = v;
     }
-    if (zero_line) {
-      double sx = 0.0, sy = 0.0;
-      for (int j = 0; j < ny; ++j) {
-        sx += (double)d[j * tl + c].x;
-        sy += (double)d[j * tl + c].y;
-      }
-      const T mx = (T)(sx / ny), my = (T)(sy / ny);
-      for (int j = 0; j < ny; ++j) {
-        d[j * tl + c].x -= mx;
-        d[j * tl + c].y -= my;
-      }
-    }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < ny * tl; idx += blockDim.x) {
-    const int j = idx >> tl2, cc = idx & (tl - 1);
-    if (kx0 + cc < nxh) spec[base + (size_t)j * nxh + cc] = d[idx];
+  if (zero_line) {
+    double sx = 0.0, sy = 0.0;
+    for (int jj = 0; jj < ny; ++jj) {
+      sx += (double)col[jj * stride].x;
+      sy += (double)col[jj * stride].y;
+    }
+    const T mx = (T)(sx / ny), my = (T)(sy / ny);
+    for (int jj = 0; jj < ny; ++jj) {
+      col[jj * stride].x -= mx;
+      col[jj * stride].y -= my;
+    }
   }
 }
 
@@ -962,13 +967,7 @@ size_t zpass_smem_limit() {
 
 template <typename T>
 cudaError_t set_smem_limits() {
-  cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, k_ythomas<T>);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ythomas<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSmemPerCta - a.sharedSizeBytes));
-  if (e == cudaSuccess) e = set_rhs_smem_limit();
-  return e;
+  return set_rhs_smem_limit();
 }
 
 template <typename T>
@@ -1057,25 +1056,11 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
 }
 
 template <typename T>
-size_t ythomas_smem(int ny, int tl) {
-  return sizeof(cpx<T>) * (size_t)ny * tl + sizeof(T) * (size_t)tl * (ny + 1);
-}
-
-// kx lines per CTA: 256-byte rows of the tile when it fits, fewer for tall ny
-template <typename T>
-int ythomas_lines(int ny) {
-  int tl = 256 / (int)sizeof(cpx<T>);
-  while (tl > 1 && ythomas_smem<T>(ny, tl) > 100 * 1024) tl /= 2;
-  return tl;
-}
-
-template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* off, const int* len, T a,
                            const DevScalars* sc, cudaStream_t st) {
   const int nxh = g.nx / 2 + 1;
-  const int tl = ythomas_lines<T>(g.ny);
-  const int grid = g.nz * ((nxh + tl - 1) / tl);
-  k_ythomas<T><<<grid, 128, ythomas_smem<T>(g.ny, tl), st>>>(g, spec, tab, off, len, a, tl, sc);
+  const dim3 grid((nxh + 127) / 128, g.nz);
+  k_ythomas<T><<<grid, 128, 0, st>>>(g, spec, tab, off, len, a, sc);
   return cudaGetLastError();
 }
 
