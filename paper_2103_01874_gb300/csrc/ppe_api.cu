@@ -1217,7 +1217,9 @@ ppe_status info_from(ppe_plan_t P, const DevScalars& h, ppe_info* info) {
   // (an open top has no compatibility condition)
   if (h.f_ran && P->opt.compat_tol > 0 && !P->gd.top_open) incompatible = fabs(h.f_sum / n) > P->opt.compat_tol * fmax;
   if (P->fp32) {
-    info->sweeps = h.sweeps;
+    // max_sweeps = 0 applies no correction; the device test that follows the
+    // fused correction-and-residual kernel counts that pass as one sweep
+    info->sweeps = P->opt.max_sweeps == 0 ? 0 : h.sweeps;
     if (h.last_slot >= 0 && fmax > 0)
       info->rel_residual = __builtin_bit_cast(double, h.rmax_bits[h.last_slot]) / fmax;
     else

@@ -28,6 +28,7 @@ def test_error_per_sweep(case, k, vel_tol, p_tol):
     from _gpu_util import project_gpu
     fl, ref = case
     res, info = project_gpu(fl, precision=ppe.FP32_REFINE, refine_tol=0.0, max_sweeps=k)
+    assert info.sweeps == k  # no tolerance: exactly max_sweeps corrections
     for key in ("u", "v", "w"):
         assert _err(res[key], ref[key]) <= vel_tol, key
     # p up to a constant
