@@ -256,6 +256,20 @@ def run_gpu(args):
         plan.profile(False)
         return max_over_ranks(ms, dist, dev), kt
 
+    def step_latency(plan, runs=60):
+        """Device time of each of `runs` back-to-back projections (one CUDA event
+        between consecutive ones on the plan's stream): median, p99 and extremes."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(runs + 1)]
+        ev[0].record(stream)
+        for i in range(runs):
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt,
+                         out["p"], out["u"], out["v"], out["w"])
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        t = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(runs))
+        return {"runs": runs, "median_ms": statistics.median(t), "p99_ms": t[min(runs - 1, math.ceil(0.99 * runs) - 1)],
+                "min_ms": t[0], "max_ms": t[-1]}
+
     steps, warmup = args.steps, args.warmup
     forms = set(args.forms.split(","))
     plan32 = ppe.Plan(NX, NY, NZ, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, refine_tol=1e-10,
@@ -263,6 +277,7 @@ def run_gpu(args):
     with ClockSampler(dev.index if world > 1 else 0) as clk:
         ms32, _ = timed(plan32, steps, warmup)
     clocks = clk.summary()
+    lat32 = step_latency(plan32)
     info32 = plan32.info(allow_not_converged=True)
     # per-kernel event timing over a second timed region of the same steps
     ms32p, kt32 = timed(plan32, steps, 1, profile=True) if args.kernel_times else (0.0, {})
@@ -373,6 +388,7 @@ def run_gpu(args):
         "gpu_launches": int(sum(v[0] for v in kt32.values()) * steps // max(1, steps)),
         "gpu_launches_note": "kernels per timed region of the headline form (profiled re-run of the same steps)",
         "profiled_ms_per_step": ms32p / steps,
+        "per_step": lat32,
     }
     if args.unsplit:
         res["unsplit"] = run_unsplit(plan32, d, out, fl, per_step32, stream)

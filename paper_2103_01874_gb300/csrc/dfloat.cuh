@@ -40,7 +40,8 @@
 
 namespace ppe {
 
-struct df {
+// 8-byte aligned, so that a pair moves as one 64-bit load or store
+struct alignas(8) df {
   float hi, lo;
 };
 
