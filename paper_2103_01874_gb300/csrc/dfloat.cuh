@@ -24,9 +24,12 @@
 // d2df(x): hi = x truncated to 24 significant bits (exponent rebias and
 // mantissa shift on the bit pattern), lo = the remaining 29 mantissa bits as an
 // integer, converted with one int->float conversion and scaled by 2^(e-1075).
-// df2d(a): exact double of hi from its bits, plus lo expressed in units of the
-// double ulp of hi (a float scaling by a power of two and one float->int
-// conversion) added to the bit pattern.  Both use only integer and FP32 ops.
+// df2d(a): the exact doubles of hi and lo from their bit patterns, added by
+// one FP64 add (correctly rounded; four per cell in the correction, well
+// within the FP64 pipe those kernels otherwise leave idle).  df2d_alu(a), for
+// kernels whose FP64 pipe is busy: exact double of hi from its bits, plus lo
+// expressed in units of the double ulp of hi (a float scaling by a power of
+// two and one float->int conversion) added to the bit pattern.
 #pragma once
 #include <math.h>
 #include <stdint.h>
@@ -212,8 +215,26 @@ PPE_HD df d2df(double x) {
   return r;
 }
 
-// pair -> IEEE double (see header comment).  Relative error ~2^-53.
-PPE_HD double df2d(df a) {
+// exact double of a float from its bit pattern: exponent rebias 127 -> 1023
+// and the 23 mantissa bits moved to the top of the 52 (zero for |x| < 2^-126)
+PPE_HD uint64_t f2d_bits(float x) {
+  const uint32_t b = f_bits(x);
+  const uint32_t m = b & 0x7FFFFFFFu;
+  if (m < 0x00800000u) return (uint64_t)(b & 0x80000000u) << 32;
+  const uint32_t hw = ((m >> 3) + 0x38000000u) | (b & 0x80000000u);
+  return ((uint64_t)hw << 32) | (uint64_t)(b << 29);
+}
+
+// pair -> IEEE double: the exact doubles of hi and lo added once, so the
+// result is hi + lo correctly rounded (one FP64 add, on a pipe the pair
+// kernels otherwise leave idle, in place of a float -> int conversion and
+// the integer carry of the previous form)
+PPE_HD double df2d(df a) { return d_from(f2d_bits(a.hi)) + d_from(f2d_bits(a.lo)); }
+
+// pair -> IEEE double with integer and FP32 operations only (see header
+// comment), for kernels whose FP64 pipe is already the limit.  Relative error
+// ~2^-53.
+PPE_HD double df2d_alu(df a) {
   a = fast_two_sum(a.hi, a.lo);
   const uint32_t hb = f_bits(a.hi);
   const uint32_t eh = (hb >> 23) & 0xFFu;  // biased float exponent of hi

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         const int idx = b0 + u * blockDim.x + threadIdx.x;
         if (idx >= lpb * nx) continue;
         const int ll = (int)fdiv(idx, g.fd_nx);
-        line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d(v[u]) : (T)df_to_f(v[u]);
+        line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d_alu(v[u]) : (T)df_to_f(v[u]);
         fsum = df_addz(fsum, v[u]);
       }
     }

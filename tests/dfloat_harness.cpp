@@ -30,10 +30,11 @@ int main() {
       std::scanf("%la", &x);
       df r = d2df(x);
       std::printf("%a %a\n", (double)r.hi, (double)r.lo);
-    } else if (!std::strcmp(op, "df2d")) {
+    } else if (!std::strcmp(op, "df2d") || !std::strcmp(op, "df2d_alu")) {
       double h, l;
       std::scanf("%la %la", &h, &l);
-      std::printf("%a\n", df2d(df{(float)h, (float)l}));
+      const df a{(float)h, (float)l};
+      std::printf("%a\n", op[4] ? df2d_alu(a) : df2d(a));
     } else {
       double ah, al, bh, bl;
       std::scanf("%la %la %la %la", &ah, &al, &bh, &bl);

@@ -57,10 +57,11 @@ def test_d2df_exactness(harness):
         assert err <= EPS48 * abs(Q(x)), (x, hi, lo)
 
 
-def test_df2d_roundtrip(harness):
+@pytest.mark.parametrize("conv", ["df2d", "df2d_alu"])
+def test_df2d_roundtrip(harness, conv):
     xs = samples(seed=1)
     pairs = harness([f"d2df {x.hex()}" for x in xs])
-    back = harness([f"df2d {p}" for p in pairs])
+    back = harness([f"{conv} {p}" for p in pairs])
     for x, p, b in zip(xs, pairs, back):
         hi, lo = (float.fromhex(t) for t in p.split())
         y = float.fromhex(b)
@@ -70,7 +71,8 @@ def test_df2d_roundtrip(harness):
         assert abs(Q(y) - Q(x)) <= EPS48 * abs(Q(x))
 
 
-def test_df2d_power_of_two_borrow(harness):
+@pytest.mark.parametrize("conv", ["df2d", "df2d_alu"])
+def test_df2d_power_of_two_borrow(harness, conv):
     """A negative lo below a power-of-two hi counts in the lower binade."""
     cases = []
     for e in (-20, 0, 7, 40):
@@ -78,7 +80,7 @@ def test_df2d_power_of_two_borrow(harness):
         for lo in (-h * 2.0 ** -26, -h * 2.0 ** -30, h * 2.0 ** -26, -h * 3 * 2.0 ** -27):
             cases.append((h, f32(lo)))
             cases.append((-h, -f32(lo)))
-    out = harness([f"df2d {h.hex()} {lo.hex()}" for h, lo in cases])
+    out = harness([f"{conv} {h.hex()} {lo.hex()}" for h, lo in cases])
     for (h, lo), line in zip(cases, out):
         y = float.fromhex(line)
         exact = Q(h) + Q(lo)
