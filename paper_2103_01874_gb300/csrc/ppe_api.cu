@@ -794,6 +794,12 @@ ppe_status ppe_set_stream(ppe_plan_t P, void* stream) {
 
 void ppe_destroy(ppe_plan_t P) {
   if (!P) return;
+  // nothing of the plan may be in flight when its memory is freed
+  if (P->acin) {
+    cudaStreamSynchronize(P->acin);
+    cudaStreamSynchronize(P->acout);
+  }
+  cudaStreamSynchronize(P->stream);
   cudaFree(P->spec);
   cudaFree(P->tw_x);
   cudaFree(P->tw_z);
@@ -816,11 +822,6 @@ void ppe_destroy(ppe_plan_t P) {
   if (P->refine_exec) cudaGraphExecDestroy(P->refine_exec);
   if (P->project_exec) cudaGraphExecDestroy(P->project_exec);
   for (int i = 0; i < 12; ++i) cudaFree(P->io[i]);
-  if (P->acin) {
-    cudaStreamSynchronize(P->acin);
-    cudaStreamSynchronize(P->acout);
-  }
-  cudaStreamSynchronize(P->stream);
   for (int b = 0; b < 2; ++b) {
     for (int i = 0; i < 9; ++i) cudaFree(P->aio[b][i]);
     if (P->aev_in[b]) cudaEventDestroy(P->aev_in[b]);

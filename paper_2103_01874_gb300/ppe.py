@@ -249,6 +249,7 @@ class Plan:
         self.grid = Grid(nx, ny, nz, lx, ly, lz)
         self.bc_top = BC_WALL if bc_top is None else bc_top
         self.opts = Options(precision, face_rule, refine_tol, max_sweeps, compat_tol, self.bc_top)
+        self._async_refs = []  # host buffers of enqueued project_host_async calls
         h = c_void_p()
         _check(lib().ppe_plan(ctypes.byref(h), ctypes.byref(self.grid), ctypes.byref(self.opts),
                               c_void_p(_stream_handle(stream))), "ppe_plan")
@@ -307,10 +308,13 @@ class Plan:
         buffers must stay untouched until host_wait()."""
         fc = self._fields(_hptr, u, v, w, S, rho, p_n, p_nm1, dt, p, u_out, v_out, w_out, f, rho0)
         _check(lib().ppe_project_host_async(self._h, ctypes.byref(fc)), "ppe_project_host_async")
+        # the copies read and write these buffers until host_wait(): keep them alive
+        self._async_refs.append((u, v, w, S, rho, p_n, p_nm1, p, u_out, v_out, w_out, f))
 
     def host_wait(self, allow_not_converged=False, allow_incompatible=False):
         """Wait for the enqueued host projections (ppe_host_wait)."""
         code = lib().ppe_host_wait(self._h)
+        self._async_refs.clear()
         if (code == 5 and allow_not_converged) or (code == 3 and allow_incompatible):
             return code
         _check(code, "ppe_host_wait")
@@ -379,8 +383,9 @@ class Plan:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            lib().ppe_destroy(self._h)
+            lib().ppe_destroy(self._h)  # waits for the plan's streams
             self._h = c_void_p()
+            self._async_refs = []
 
     def __del__(self):
         try:

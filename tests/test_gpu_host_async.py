@@ -77,3 +77,28 @@ def test_missing_argument_is_refused():
             plan.project_host_async(hin["u"], hin["v"], hin["w"], hin["S"], hin["rho"], hin["p_n"], hin["p_nm1"],
                                     fl.dt, hout["p"], hout["u"], hout["u"], hout["w"])  # v_out of the wrong shape
         assert plan.host_wait() == 0
+
+
+def test_plan_keeps_the_input_buffers_of_enqueued_calls():
+    """Inputs passed as temporaries stay valid until host_wait: the binding
+    holds them, so recycling pinned memory in between changes no result."""
+    import torch
+    fls = [fields.make_fields(*SHAPE, seed=90 + s, recipe="multimode", width=3.0) for s in range(3)]
+    with ppe.Plan(*SHAPE, fls[0].lx, fls[0].ly, fls[0].lz, precision=ppe.FP32_REFINE) as plan:
+        ref = []
+        for fl in fls:
+            hin, hout = _host(fl)
+            plan.project_host(*_args(fl, hin, hout))
+            ref.append({k: t.numpy().copy() for k, t in hout.items()})
+        outs = []
+        for fl in fls:
+            hin, hout = _host(fl)
+            plan.project_host_async(*_args(fl, hin, hout))
+            outs.append(hout)
+            del hin  # only the plan refers to the inputs now
+            junk = [torch.full((fl.nz, fl.ny, fl.nx), 7.0, dtype=torch.float64).pin_memory() for _ in range(8)]
+            del junk
+        assert plan.host_wait() == 0
+        for r, hout in zip(ref, outs):
+            for k in r:
+                assert np.array_equal(hout[k].numpy(), r[k]), k
