@@ -266,7 +266,9 @@ ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields*
  * failed for the last solve's f (info is filled in both cases), else PPE_OK. */
 ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
 
-/* Free the workspace.  NULL is ignored. */
+/* Wait for the plan's streams (its own and, if ppe_project_host_async was used,
+ * its copy streams; pending host-buffer calls complete but their status is
+ * dropped), then free the workspace and the staging buffers.  NULL is ignored. */
 void ppe_destroy(ppe_plan_t plan);
 
 /* Launch-shape tuning of a plan (what an autotuner sweeps).  Every field is a
