@@ -321,9 +321,11 @@ __global__ void k_finish_sums(GridDev g, DevScalars* sc) { finish_sums(sc, g); }
 // as do the x neighbours), and the y-face values never go through shared
 // memory; the x faces are exchanged through shared memory for the cell
 // divergence.  Faces between two stacks are evaluated by both (same bits).
-template <int S, int RULE, bool PROJ>
-__global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
-    k_rhs_stack(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int kc) {
+// INT: the tile and its halo lines lie strictly inside the walls (no wall or
+// open-top face, every line in range), so the boundary branches drop out.
+template <int S, int RULE, bool PROJ, bool INT>
+__device__ __forceinline__ void rhs_stack_body(const GridDev& g, const StencilIn& in, DevScalars* sc,
+                                               const RhsOut& out, int kc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nstk = kRhsThreads / nx;
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
   const int ip = (i + 1 == nx) ? 0 : i + 1;
   bool cv[S];
 #pragma unroll
-  for (int l = 0; l < S; ++l) cv[l] = active && (j0 + jb + l < ny);
+  for (int l = 0; l < S; ++l) cv[l] = active && (INT || j0 + jb + l < ny);
 
   auto cell = [&](int kk, int j) -> uint32_t { return (uint32_t)kk * plane + (uint32_t)(j * nx + i); };
   uint32_t coff[S];  // offsets of the own lines within a plane
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
       const int j = h ? j0 + tj : j0 - 1;
       const int row = h ? nl - 1 : 0;
       df pv = {0.0f, 0.0f}, rv = {1.0f, 0.0f};
-      if (j >= 0 && j < ny) {
+      if (INT || (j >= 0 && j < ny)) {
         const uint32_t c = (uint32_t)kk * plane + (uint32_t)(j * nx + x);
         pv = phat_of(__ldg(in.pn + c), __ldg(in.pnm1 + c));
         rv = d2df(__ldg(in.rho + c));
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
 #pragma unroll
     for (int f = 0; f <= S; ++f) {
       const int j = j0 + jb + f;
-      vs_[f] = (active && j <= ny) ? __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)(j * nx + i))) : 0.0;
+      vs_[f] = (active && (INT || j <= ny)) ? __ldg(in.v + ((uint32_t)k * vplane + (uint32_t)(j * nx + i))) : 0.0;
     }
   };
 
@@ -489,19 +491,19 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     for (int f = 0; f <= S; ++f) {  // face between tile lines jb+f-1 and jb+f
       QY[f] = {0.0f, 0.0f};
       const int j = j0 + jb + f;
-      if (!active || j > ny) continue;
+      if (!active || (!INT && j > ny)) continue;
       const df vs = d2df(vs_[f]);
       const uint32_t cvv = (uint32_t)k * vplane + (uint32_t)(j * nx + i);
       // a face belongs to the stack holding the line above it; the top wall to
       // the stack holding line ny - 1
-      const bool own = (f < S && j < ny) || (j == ny && f >= 1);
-      if (j == ny && g.top_open) {  // open top: p = 0 on the face, ghost -p_hat above
+      const bool own = INT ? (f < S) : ((f < S && j < ny) || (j == ny && f >= 1));
+      if (!INT && j == ny && g.top_open) {  // open top: p = 0 on the face, ghost -p_hat above
         const df rl = (f == 0) ? R[(jb) * nx + i] : RC[f > 0 ? f - 1 : 0];
         const df pl = (f == 0) ? P[(jb) * nx + i] : PC[f > 0 ? f - 1 : 0];
         const FaceOut fo = face_q(rl, rl, pl, df_neg(pl), vs, K.cy, K.gy, K, rule);
         QY[f] = fo.q;
         if (PROJ && own) out.vpre[cvv] = fo.upre;
-      } else if (j == 0 || j == ny) {  // wall
+      } else if (!INT && (j == 0 || j == ny)) {  // wall
         QY[f] = df_norm(df_mulz(K.cy, vs));
         if (PROJ && own) out.vpre[cvv] = vs;
         if (own) {
@@ -572,6 +574,18 @@ __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     sc->rhs_tiles = ntile;
     sc->rhs_chunks = (nz + kc - 1) / kc;
   }
+}
+
+template <int S, int RULE, bool PROJ>
+__global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
+    k_rhs_stack(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int kc) {
+  const int tj = (kRhsThreads / g.nx) * S;
+  const int ntile = (g.ny + tj - 1) / tj;
+  const int j0 = (int)(blockIdx.x % ntile) * tj;
+  if (j0 > 0 && j0 + tj < g.ny)  // uniform over the CTA
+    rhs_stack_body<S, RULE, PROJ, true>(g, in, sc, out, kc);
+  else
+    rhs_stack_body<S, RULE, PROJ, false>(g, in, sc, out, kc);
 }
 
 // Lines per tile: the stack form (nx <= 256) has 256 / nx stacks of `lines`
