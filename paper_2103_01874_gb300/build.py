@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and out.strip():
                 print(out)
     tmp = LIB + ".tmp"
-    run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost a pointer test when no tool is attached
+
 #include "../../include/ppe.h"
 #include "ppe_internal.h"
 
@@ -310,13 +312,25 @@ void prof_end(ppe_plan_t P, int r) {
 }
 
 // Launch with optional per-kernel event bracketing.
+// Every launch of the path: an NVTX range named after the kernel (for
+// timeline tools), the optional per-kernel event timing, the status check.
 #define PPE_LAUNCH(P, ID, expr)             \
   do {                                      \
+    nvtxRangePushA(kKernelNames[ID]);       \
     const int _r = prof_begin(P, ID);       \
     ppe_status _s = cuda_status(expr);      \
     prof_end(P, _r);                        \
+    nvtxRangePop();                         \
     if (_s != PPE_OK) return _s;            \
   } while (0)
+
+// NVTX range over one call of the C ABI
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define PPE_TRY(expr)                      \
   do {                                     \
@@ -916,6 +930,7 @@ int ppe_profile_read(ppe_plan_t P, ppe_kernel_time* out, int max_entries) {
 
 ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double* w, const double* S,
                    const double* rho, const double* p_n, const double* p_nm1, double rho0, double dt, double* f) {
+  NvtxRange _nvtx("ppe_rhs");
   if (!P || !u || !v || !w || !S || !rho || !p_n || !p_nm1 || !f || !(dt > 0)) return PPE_ERR_INVALID_ARG;
   StencilIn in = make_in(P, u, v, w, S, rho, p_n, p_nm1, dt);
   const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
@@ -928,6 +943,7 @@ ppe_status ppe_rhs(ppe_plan_t P, const double* u, const double* v, const double*
 }
 
 ppe_status ppe_solve(ppe_plan_t P, const double* f, double* p) {
+  NvtxRange _nvtx("ppe_solve");
   if (!P || !f || !p) return PPE_ERR_INVALID_ARG;
   StencilIn in;
   memset(&in, 0, sizeof(in));
@@ -953,6 +969,7 @@ ppe_status ppe_solve(ppe_plan_t P, const double* f, double* p) {
 ppe_status ppe_correct(ppe_plan_t P, const double* u, const double* v, const double* w, const double* rho,
                        const double* p, const double* p_n, const double* p_nm1, double rho0, double dt,
                        double* u_out, double* v_out, double* w_out) {
+  NvtxRange _nvtx("ppe_correct");
   if (!P || !u || !v || !w || !rho || !p || !p_n || !p_nm1 || !u_out || !v_out || !w_out || !(dt > 0))
     return PPE_ERR_INVALID_ARG;
   StencilIn in = make_in(P, u, v, w, nullptr, rho, p_n, p_nm1, dt);
@@ -964,6 +981,7 @@ ppe_status ppe_correct(ppe_plan_t P, const double* u, const double* v, const dou
 }
 
 ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
+  NvtxRange _nvtx("ppe_project");
   if (!P || !F || !F->u || !F->v || !F->w || !F->S || !F->rho || !F->p_n || !F->p_nm1 || !F->p || !F->u_out ||
       !F->v_out || !F->w_out || !(F->dt > 0))
     return PPE_ERR_INVALID_ARG;
@@ -996,6 +1014,7 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
 }
 
 ppe_status ppe_project_unsplit(ppe_plan_t P, const ppe_fields* F, double tol, int max_iter) {
+  NvtxRange _nvtx("ppe_project_unsplit");
   if (!P || !F || !F->u || !F->v || !F->w || !F->S || !F->rho || !F->p || !F->u_out || !F->v_out || !F->w_out ||
       !(F->dt > 0) || !(tol >= 0) || max_iter < 0 || max_iter > 100000)
     return PPE_ERR_INVALID_ARG;
@@ -1136,6 +1155,7 @@ ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, co
 }
 
 ppe_status ppe_batch_launch(ppe_batch_t B) {
+  NvtxRange _nvtx("ppe_batch_launch");
   if (!B) return PPE_ERR_INVALID_ARG;
   PPE_TRY(cudaGraphLaunch(B->exec, B->stream));
   return PPE_OK;
@@ -1158,6 +1178,7 @@ ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields*
 }
 
 ppe_status ppe_project_host(ppe_plan_t P, const ppe_fields* H) {
+  NvtxRange _nvtx("ppe_project_host");
   if (!P || !H || !H->u || !H->v || !H->w || !H->S || !H->rho || !H->p_n || !H->p_nm1 || !H->p || !H->u_out ||
       !H->v_out || !H->w_out || !(H->dt > 0))
     return PPE_ERR_INVALID_ARG;
@@ -1249,6 +1270,7 @@ ppe_status async_retire(ppe_plan_t P, int b) {
 }  // namespace
 
 ppe_status ppe_project_host_async(ppe_plan_t P, const ppe_fields* H) {
+  NvtxRange _nvtx("ppe_project_host_async");
   if (!P || !H || !H->u || !H->v || !H->w || !H->S || !H->rho || !H->p_n || !H->p_nm1 || !H->p || !H->u_out ||
       !H->v_out || !H->w_out || !(H->dt > 0))
     return PPE_ERR_INVALID_ARG;

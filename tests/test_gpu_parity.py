@@ -171,6 +171,29 @@ from _gpu_util import dev_fields, project_gpu, to_dev  # noqa: E402
 
 
 @pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
+def test_repeated_projections_are_bit_identical(precision):
+    """Determinism: sums are totalled in a fixed order and the maxima use
+    integer atomics on bit patterns, so the same inputs give the same bits on
+    every call (here three calls through the captured graph of one plan)."""
+    import torch
+    fl = fields.make_fields(64, 48, 64, seed=23, recipe="multimode", width=4.0, rho_g=60.0)
+    d = dev_fields(fl)
+    outs = []
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=precision) as plan:
+        for _ in range(3):
+            o = [torch.empty(fl.shape, dtype=torch.float64, device="cuda"), torch.empty_like(d["u"]),
+                 torch.empty_like(d["v"]), torch.empty_like(d["w"])]
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, *o)
+            torch.cuda.synchronize()
+            outs.append([t.cpu().numpy() for t in o])
+            info = plan.info()
+            outs[-1].append(np.array([info.rel_residual, info.f_max, info.sweeps]))
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
 @pytest.mark.parametrize("grid", [(48, 24, 36), (64, 32, 64)])
 def test_tuning_does_not_change_results(precision, grid):
     """Launch shapes (tile sizes, marching chunk) change no bit of the outputs,
