@@ -7,8 +7,17 @@
 namespace ppe {
 
 // keep_rho0: leave rho_0 as the last right-hand side set it (ppe_solve).
-__global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0) {
+// out_p non-null: also record the ppe_project outputs (read by the fused
+// correction check, so that a captured refinement graph serves every call).
+__global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, double* out_p,
+                               double* out_u, double* out_v, double* out_w) {
   if (threadIdx.x != 0) return;
+  if (out_p) {
+    sc->out_p = out_p;
+    sc->out_u = out_u;
+    sc->out_v = out_v;
+    sc->out_w = out_w;
+  }
   // rho0 <= 0: start the min-reduction at +inf
   if (!keep_rho0)
     sc->rho0_bits = rho0 > 0.0 ? (unsigned long long)__double_as_longlong(rho0) : 0x7FF0000000000000ull;
@@ -204,14 +213,6 @@ __global__ void k_refine_check(DevScalars* sc, int smax, int off, cudaGraphCondi
   if (use_handle) cudaGraphSetConditional(handle, cont);
 }
 
-__global__ void k_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w) {
-  if (threadIdx.x == 0) {
-    sc->out_p = p;
-    sc->out_u = u;
-    sc->out_v = v;
-    sc->out_w = w;
-  }
-}
 
 // Eq. (33) from u_pre as in k_correct_pre, with p as pairs, plus the residual
 // r = f - L p of that same p at every cell (max into rmax[iter + 1]), so that the
@@ -342,8 +343,9 @@ cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st) {
-  k_init_scalars<<<1, 32, 0, st>>>(sc, rho0, tol, keep_rho0);
+cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st,
+                                double* out_p, double* out_u, double* out_v, double* out_w) {
+  k_init_scalars<<<1, 32, 0, st>>>(sc, rho0, tol, keep_rho0, out_p, out_u, out_v, out_w);
   return cudaGetLastError();
 }
 
@@ -375,11 +377,6 @@ cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const Dev
                                 double* v_out, double* w_out, cudaStream_t st) {
   const size_t total = (size_t)g.nz * (g.ny + 1) * g.nx;
   k_correct_full<<<grid_for(total, (size_t)152 * 64), 256, 0, st>>>(g, in, sc, u_out, v_out, w_out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w, cudaStream_t st) {
-  k_set_outputs<<<1, 32, 0, st>>>(sc, p, u, v, w);
   return cudaGetLastError();
 }
 

@@ -274,13 +274,13 @@ ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_E
 // Kernel names reported by ppe_profile_read.
 enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
                 K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_VC_SETUP, K_VC_APPLY, K_VC_UPDATE,
-                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_DIV_S, K_CONST, K_OUTPUTS, K_COUNT };
+                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_DIV_S, K_CONST, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
                                            "k_xfwd_resid", "k_zfft_fwd", "k_ysolve", "k_zfft_inv",
                                            "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
                                            "k_df_to_d", "k_vc_setup", "k_vc_apply", "k_vc_update",
                                            "k_vc_dots", "k_vc_pupdate", "k_vc_scalars", "k_vc_correct",
-                                           "k_div_constraint", "k_make_const", "k_set_outputs"};
+                                           "k_div_constraint", "k_make_const"};
 constexpr int kProfMax = 16384;
 
 int prof_begin(ppe_plan_t P, int id) {
@@ -987,12 +987,13 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
     return PPE_ERR_INVALID_ARG;
   StencilIn in = make_in(P, F->u, F->v, F->w, F->S, F->rho, F->p_n, F->p_nm1, F->dt);
   const size_t n = (size_t)P->g.nx * P->g.ny * P->g.nz;
-  PPE_LAUNCH(P, K_INIT, launch_init_scalars(P->sc, F->rho0, P->opt.refine_tol, 0, P->stream));
+  PPE_LAUNCH(P, K_INIT, P->fp32 ? launch_init_scalars(P->sc, F->rho0, P->opt.refine_tol, 0, P->stream, F->p,
+                                                       F->u_out, F->v_out, F->w_out)
+                                 : launch_init_scalars(P->sc, F->rho0, P->opt.refine_tol, 0, P->stream));
   if (!(F->rho0 > 0)) PPE_LAUNCH(P, K_RHO_MIN, launch_rho_min(F->rho, n, P->sc, P->stream));
   PPE_LAUNCH(P, K_CONST, launch_make_const(P->gd, P->sc, F->dt, P->stream));
   ppe_status s;
   if (P->fp32) {
-    PPE_LAUNCH(P, K_OUTPUTS, launch_set_outputs(P->sc, F->p, F->u_out, F->v_out, F->w_out, P->stream));
     PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre, P->tj, P->kc,
                                     P->stream));
     PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr,

@@ -39,7 +39,7 @@ struct DevScalars {
   int sweeps;                                   // sweeps run
   double tol;                                   // refinement tolerance (relative)
   StencilConst K;                               // stencil constants of the current call
-  double* out_p;                                // ppe_project outputs, set per call (k_set_outputs)
+  double* out_p;                                // ppe_project outputs, set per call (k_init_scalars)
   double* out_u;
   double* out_v;
   double* out_w;
@@ -173,7 +173,9 @@ size_t zpass_smem_limit();  // the same for the z pass
 cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_g, const double* comp_l,
                                   const double* mdot, const double* rho_g, const double* rho_l,
                                   const unsigned char* mask, double* S, double* rho, cudaStream_t st);
-cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st);
+cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st,
+                                double* out_p = nullptr, double* out_u = nullptr, double* out_v = nullptr,
+                                double* out_w = nullptr);
 cudaError_t launch_set_rho0(DevScalars* sc, double rho0, cudaStream_t st);
 // Forms sc->K from sc->rho0, dt and the grid (one thread).
 cudaError_t launch_make_const(const GridDev& g, DevScalars* sc, double dt, cudaStream_t st);
@@ -189,7 +191,6 @@ cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const Dev
 cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st);
 // Writes the per-call output pointers of ppe_project into sc (so that graphs
 // captured once can run with any outputs).
-cudaError_t launch_set_outputs(DevScalars* sc, double* p, double* u, double* v, double* w, cudaStream_t st);
 // Eq. (33) from u_pre and p (pairs) fused with the residual r = f - L p of the
 // same p into rmax[iter + 1]; outputs through sc->out_*.
 cudaError_t launch_correct_check(const GridDev& g, const df* upre, const df* vpre, const df* wpre, const df* pdf,
