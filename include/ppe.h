@@ -61,14 +61,19 @@ typedef enum {
     PPE_ERR_INCOMPATIBLE_RHS = 3,
     PPE_ERR_OUT_OF_MEMORY = 4,
     PPE_ERR_NOT_CONVERGED = 5,
-    PPE_ERR_TIMEOUT = 6,
+    PPE_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (see ppe_get_info) */
     PPE_ERR_CUDA = 7
 } ppe_status;
 
-/* Arithmetic of the direct solve.  PPE_FP64: every step in FP64.
- * PPE_FP32_REFINE: the transforms and the tridiagonal solve run in FP32 inside
- * an iterative refinement whose residual r = f - L p and solution update are
- * FP64; the right-hand side and the velocity correction stay FP64. */
+/* Arithmetic of the projection.  Every field crosses the boundary as IEEE
+ * FP64.  The stencils -- the Eq. (34) right-hand side, the refinement residual
+ * r = f - L p, the p update and the Eq. (33) correction -- run in both forms
+ * in double-float pairs (two FP32 numbers carrying about 48 significant bits,
+ * relative rounding ~2^-48 = 3.6e-15 per operation), because FP64 issues at
+ * about 1/64 of the FP32 rate on this GPU.
+ * PPE_FP64: the transforms and the tridiagonal y solve in native FP64.
+ * PPE_FP32_REFINE: the transforms and the y solve in FP32 inside an iterative
+ * refinement whose residual and update are formed in the pairs above. */
 typedef enum { PPE_FP64 = 0, PPE_FP32_REFINE = 1 } ppe_precision;
 
 /* Face density rho_f: arithmetic mean (default) or harmonic mean of the two
@@ -271,19 +276,38 @@ ppe_status ppe_get_info(ppe_plan_t plan, ppe_info* info);
  * dropped), then free the workspace and the staging buffers.  NULL is ignored. */
 void ppe_destroy(ppe_plan_t plan);
 
-/* Launch-shape tuning of a plan (what an autotuner sweeps).  Every field is a
- * tile size of one pass; results do not depend on them.
+/* Schedule and launch-shape tuning of a plan (what an autotuner sweeps).
  *   rhs_lines   y-lines per CTA of the right-hand-side kernel: 1, 2, 4 or 8
  *   rhs_planes  z-planes each of its CTAs marches through: 1 .. nz
  *   x_lines     x-lines per CTA of the x transforms: power of two in 1 .. 64
  *   z_cols      kx columns per CTA of the z transforms: 1, 2, 4, 8 or 16
  *   y_cols      kx columns per CTA of the y pass (FP32_REFINE): 1 .. 32, power of two
+ *   spectral    schedule of the z and y steps of the solve (PPE_SPECTRAL_*):
+ *               LEGACY  three passes (z, y, inverse z) on the spectrum stored
+ *                       [kz][j][kx], kx fastest; every plan supports it;
+ *               FUSED   one pass per kx plane: a thread-block cluster whose
+ *                       shared memory holds the plane (tiles moved by bulk
+ *                       tensor copies, y lines read across the cluster's CTAs);
+ *               PENCIL  three persistent passes on the spectrum stored
+ *                       [kx][kz][j], each tile (32 KB) moved in and out by bulk
+ *                       copies (a tensor map for the z tiles) while the previous
+ *                       one is transformed.
+ *               FUSED and PENCIL serve PPE_FP32_REFINE plans with walls, ny and
+ *               nz in {32, 64, 128, 256} and nx/2 a power of two in [16, 512].
+ *               LEGACY is the default of every plan; ppe_get_tuning reports
+ *               the schedule in use.
+ * The first five are tile sizes and change no result bit.  The schedules run
+ * the same arithmetic, but the compiler may contract the FP32 products of the
+ * y pass differently, so their FP32 solves can differ in the last bits; the
+ * refined results then agree to the refinement's tolerance.
  * ppe_set_tuning returns PPE_ERR_INVALID_ARG (and changes nothing) if a value
- * is outside its range or a pass would need more than 227 KB of shared memory
- * per CTA.  Synchronises the plan's stream (captured refinement graphs are
- * rebuilt with the new shapes). */
+ * is outside its range, a schedule is not available for the plan, or a pass
+ * would need more than 227 KB of shared memory per CTA.  Synchronises the
+ * plan's stream (captured refinement graphs are rebuilt with the new
+ * schedule). */
+enum { PPE_SPECTRAL_LEGACY = 0, PPE_SPECTRAL_FUSED = 1, PPE_SPECTRAL_PENCIL = 2 };
 typedef struct {
-    int rhs_lines, rhs_planes, x_lines, z_cols, y_cols;
+    int rhs_lines, rhs_planes, x_lines, z_cols, y_cols, spectral;
 } ppe_tuning;
 ppe_status ppe_get_tuning(ppe_plan_t plan, ppe_tuning* out);
 ppe_status ppe_set_tuning(ppe_plan_t plan, const ppe_tuning* tuning);

@@ -337,10 +337,24 @@ namespace rgfft {
 
 __host__ __device__ constexpr int rows(int n) { return n + n / 16; }
 __device__ __forceinline__ int row(int e) { return e + (e >> 4); }
+// Position of element e in a line, by layout:
+//   PAD_ROWS (true):  row(e), one padding row every 16 elements;
+//   DENSE (false):    e (a buffer laid out by a bulk copy whose lines run across
+//                     columns, so that a warp's lanes touch consecutive words);
+//   XOR_ROWS (2):     e ^ ((e >> 4) & 15), a permutation within each group of
+//                     16 that needs no extra space: a line stored along a dense
+//                     row (bulk-copied) with its M/16 threads as consecutive
+//                     lanes reads and writes 16 distinct 8-byte bank slots in
+//                     both Stockham index patterns (16 t + q and t + 16 q).
+enum RowLayout { DENSE = 0, PAD_ROWS = 1, XOR_ROWS = 2 };
+template <int LAYOUT>
+__device__ __forceinline__ int rowp(int e) {
+  return LAYOUT == PAD_ROWS ? row(e) : (LAYOUT == XOR_ROWS ? (e ^ ((e >> 4) & 15)) : e);
+}
 
 // LD_SHARED: ld reads the shared buffer (the first pass then waits for all
 // reads before writing); later passes always read all before their stores.
-template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, class Ld, class St>
+template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, int PAD, class Ld, class St>
 __device__ __forceinline__ void pass(Ld& ld, St& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
   using namespace ctfft;
   constexpr int NST = nst(N, 16);
@@ -359,7 +373,7 @@ __device__ __forceinline__ void pass(Ld& ld, St& st, cpx<T>* ln, int es, int t0,
     for (int q = 0; q < R; ++q) {
       const int e = t + q * NB;
       if (S == 0) v[it][q] = ld(e);
-      else v[it][q] = ln[row(e) * es];
+      else v[it][q] = ln[rowp<PAD>(e) * es];
     }
   }
   if (S > 0 || LD_SHARED) __syncthreads();  // in place: every read of the pass before any write
@@ -381,17 +395,17 @@ __device__ __forceinline__ void pass(Ld& ld, St& st, cpx<T>* ln, int es, int t0,
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       if (S + 1 == NST) st(o + q * NS, v[it][q]);
-      else ln[row(o + q * NS) * es] = v[it][q];
+      else ln[rowp<PAD>(o + q * NS) * es] = v[it][q];
     }
   }
   if (S + 1 < NST) __syncthreads();
 }
 
-template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, class Ld, class St>
+template <typename T, bool INV, int N, int S, int TWS, bool LD_SHARED, int PAD, class Ld, class St>
 __device__ __forceinline__ void run_from(Ld& ld, St& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
   if constexpr (S < ctfft::nst(N, 16)) {
-    pass<T, INV, N, S, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
-    run_from<T, INV, N, S + 1, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
+    pass<T, INV, N, S, TWS, LD_SHARED, PAD>(ld, st, ln, es, t0, tw);
+    run_from<T, INV, N, S + 1, TWS, LD_SHARED, PAD>(ld, st, ln, es, t0, tw);
   }
 }
 
@@ -401,10 +415,10 @@ __device__ __forceinline__ void run_from(Ld& ld, St& st, cpx<T>* ln, int es, int
 // second pass (the barrier after the first pass suffices when it is written
 // before the call).  The caller synchronises after the call before reusing
 // the buffer.
-template <typename T, bool INV, int N, int TWS, bool LD_SHARED, class Ld, class St>
+template <typename T, bool INV, int N, int TWS, bool LD_SHARED, int PAD = PAD_ROWS, class Ld, class St>
 __device__ __forceinline__ void run(Ld&& ld, St&& st, cpx<T>* ln, int es, int t0, const cpx<T>* __restrict__ tw) {
   static_assert((N & (N - 1)) == 0 && N >= 16 && N <= 512, "power-of-two length");
-  run_from<T, INV, N, 0, TWS, LD_SHARED>(ld, st, ln, es, t0, tw);
+  run_from<T, INV, N, 0, TWS, LD_SHARED, PAD>(ld, st, ln, es, t0, tw);
 }
 
 template <int N> struct is_rg : std::integral_constant<bool, (N >= 16 && N <= 512 && (N & (N - 1)) == 0)> {};

@@ -228,6 +228,23 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
 // Line stride (complex elements) of the x passes' shared buffer: rgfft rows,
 // padded to 8 mod 16 so that neighbouring lines start half a bank row apart.
 __host__ __device__ constexpr int xrg_stride(int m) { return rgfft::rows(m) + ((8 - rgfft::rows(m) % 16) + 16) % 16; }
+// The same for the plane layout of the spectrum (PL): one more element (the
+// inverse pass stages X_M too) and padded to 4 mod 16, so that both the FFT
+// passes (lanes: 32/(M/16) lines of M/16 threads) and the transposing copies
+// (lanes: 8 lines x 4 kx) touch each 8-byte bank slot at most twice per warp.
+__host__ __device__ constexpr int xrg_stride_pl(int m) {
+  return (rgfft::rows(m) + 1) + ((4 - (rgfft::rows(m) + 1) % 16) + 16) % 16;
+}
+template <bool PL>
+__host__ __device__ constexpr int xstride(int m) { return PL ? xrg_stride_pl(m) : xrg_stride(m); }
+
+// Lane split of the transposing copies of the plane layout: LQ consecutive
+// lines (8, or all L when fewer) times 32/LQ consecutive kx per warp, so that a
+// warp moves 64-byte runs of one kx plane.
+struct PlaneLanes {
+  int lq, kq;
+};
+__device__ __forceinline__ PlaneLanes plane_lanes(int L) { return {L < 8 ? L : 8, 32 / (L < 8 ? L : 8)}; }
 
 // Register-staged forward x pass (FP32, nx = 2M, M a power of two; rgfft in
 // fft.cuh).  A CTA of L * M/16 threads owns L consecutive x-lines; thread
@@ -236,14 +253,15 @@ __host__ __device__ constexpr int xrg_stride(int m) { return rgfft::rows(m) + ((
 // or the residual f - L p in pair arithmetic, two cells per 16-byte load --
 // the last pass leaves Z in shared memory and the untangle writes the nx/2 + 1
 // half spectrum.  Same cell arithmetic as k_xfwd.
-template <int SRC, int M, bool OPEN>
+// PL: the spectrum in the plane layout [kx][line] (GridDev::spec_planes).
+template <int SRC, int M, bool OPEN, bool PL = false>
 __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
                                                  const df* __restrict__ pdf, cpx<float>* spec,
                                                  const cpx<float>* __restrict__ tw, int L) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
-  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xrg_stride(M);
+  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xstride<PL>(M);
   const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
   const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
   const uint32_t l0 = blockIdx.x * (uint32_t)L;
@@ -259,10 +277,13 @@ __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevSca
   if constexpr (SRC == SRC_F) {
     const double2* fl = reinterpret_cast<const double2*>(in.f + c0);
     float4* fo = fdf ? reinterpret_cast<float4*>(fdf + c0) : nullptr;
+    // a caller's f off a 16-byte boundary is read with 8-byte loads (the plane
+    // layout has no other forward pass to fall back to)
+    const bool f16 = !PL || ((uintptr_t)in.f & 15u) == 0;
     rgfft::run<T, false, M, 2, false>(
         [&](int e) -> cpx<T> {
           if (!valid) return {(T)0, (T)0};
-          const double2 x = __ldg(fl + e);
+          const double2 x = f16 ? __ldg(fl + e) : make_double2(__ldg(in.f + c0 + 2 * e), __ldg(in.f + c0 + 2 * e + 1));
           const df v0 = d2df(x.x), v1 = d2df(x.y);
           if (fo) fo[e] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
           vmax = fmaxf(vmax, fmaxf(fabsf(v0.hi), fabsf(v1.hi)));
@@ -336,9 +357,7 @@ __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevSca
   }
   __syncthreads();
   // untangle: X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, W = exp(-2 pi i/nx)
-  for (int idx = threadIdx.x; idx < L * nxh; idx += blockDim.x) {
-    const int lq = idx / nxh, kx = idx - lq * nxh;
-    if (l0 + lq >= nlines) continue;
+  auto untangle = [&](int lq, int kx) {
     const cpx<T> zk = buf[lq * LS + rgfft::row(kx == M ? 0 : kx)];
     const cpx<T> zc = buf[lq * LS + rgfft::row(kx == 0 ? 0 : M - kx)];
     const cpx<T> a = {zk.x + zc.x, zk.y - zc.y};
@@ -347,7 +366,25 @@ __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevSca
     cpx<T> X;
     X.x = (T)0.5 * (a.x + wb.y);
     X.y = (T)0.5 * (a.y - wb.x);
-    spec[(l0 + lq) * (uint32_t)nxh + kx] = X;
+    return X;
+  };
+  if constexpr (!PL) {
+    for (int idx = threadIdx.x; idx < L * nxh; idx += blockDim.x) {
+      const int lq = idx / nxh, kx = idx - lq * nxh;
+      if (l0 + lq >= nlines) continue;
+      spec[(l0 + lq) * (uint32_t)nxh + kx] = untangle(lq, kx);
+    }
+  } else {
+    // transposed store: plane kx holds the lines in order (index kx * lines + line)
+    const PlaneLanes pl = plane_lanes(L);
+    const int lane = threadIdx.x & 31, lqo = lane % pl.lq, kxo = lane / pl.lq;
+    const int ngl = L / pl.lq, ngk = (nxh + pl.kq - 1) / pl.kq;
+    for (int w = threadIdx.x >> 5; w < ngl * ngk; w += blockDim.x >> 5) {
+      const int gl = w % ngl, gk = w / ngl;
+      const int lq = gl * pl.lq + lqo, kx = gk * pl.kq + kxo;
+      if (kx >= nxh || l0 + lq >= nlines) continue;
+      spec[(uint32_t)kx * nlines + l0 + lq] = untangle(lq, kx);
+    }
   }
 }
 
@@ -832,14 +869,17 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
 // X_k and X_{M-k} read straight from the spectrum, and the last pass stores
 // (or adds) the real pairs of cells 2n, 2n+1 with one 16-byte access.  Same
 // arithmetic as k_xinv.
-template <int MODE, int M>
+// PL: the spectrum in the plane layout [kx][line]; the CTA's half spectra are
+// first copied (transposed) into the shared buffer, then the first pass reads
+// them there.
+template <int MODE, int M, bool PL = false>
 __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
                                                  double scale, const cpx<float>* __restrict__ tw, int L,
                                                  const DevScalars* sc) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
-  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xrg_stride(M);
+  constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xstride<PL>(M);
   const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
   const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
   const uint32_t line = blockIdx.x * (uint32_t)L + ll;
@@ -847,14 +887,43 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* tws = buf + L * LS;
   for (int t = threadIdx.x; t < nx; t += blockDim.x) tws[t] = tw[t];
-  const cpx<T>* X = spec + line * (uint32_t)nxh;
+  if constexpr (PL) {
+    const uint32_t l0 = blockIdx.x * (uint32_t)L;
+    const PlaneLanes pl = plane_lanes(L);
+    const int lane = threadIdx.x & 31, lqo = lane % pl.lq, kxo = lane / pl.lq;
+    const int ngl = L / pl.lq, ngk = (nxh + pl.kq - 1) / pl.kq;
+    const int nw = (int)blockDim.x >> 5;
+    // eight loads per thread in flight before their shared-memory stores
+    constexpr int U = 8;
+    for (int w0 = threadIdx.x >> 5; w0 < ngl * ngk; w0 += U * nw) {
+      cpx<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int w = w0 + u * nw;
+        const int gl = w % ngl, gk = w / ngl;
+        const int lq = gl * pl.lq + lqo, kx = gk * pl.kq + kxo;
+        v[u] = (w < ngl * ngk && kx < nxh && l0 + lq < nlines) ? spec[(uint32_t)kx * nlines + l0 + lq]
+                                                                : cpx<T>{(T)0, (T)0};
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int w = w0 + u * nw;
+        const int gl = w % ngl, gk = w / ngl;
+        const int lq = gl * pl.lq + lqo, kx = gk * pl.kq + kxo;
+        if (w < ngl * ngk && kx < nxh) buf[lq * LS + rgfft::row(kx)] = v[u];
+      }
+    }
+    __syncthreads();
+  }
+  const cpx<T>* X = PL ? nullptr : spec + line * (uint32_t)nxh;
+  const cpx<T>* Xs = buf + ll * LS;
   const uint32_t c0 = line * (uint32_t)nx;
   const df sdf = d2df(scale);
   // Z_k = E_k + i O_k, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(W^k)/2
   auto ld = [&](int k) -> cpx<T> {
     if (!valid) return {(T)0, (T)0};
-    const cpx<T> xk = X[k];
-    const cpx<T> xc = X[M - k];
+    const cpx<T> xk = PL ? Xs[rgfft::row(k)] : X[k];
+    const cpx<T> xc = PL ? Xs[rgfft::row(M - k)] : X[M - k];
     const cpx<T> e = {(T)0.5 * (xk.x + xc.x), (T)0.5 * (xk.y - xc.y)};
     const cpx<T> dd = {(T)0.5 * (xk.x - xc.x), (T)0.5 * (xk.y + xc.y)};
     cpx<T> w = tw[k];
@@ -880,12 +949,12 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
     }
   };
   if constexpr (MODE != XI_DF_ACC) {
-    rgfft::run<T, true, M, 2, false>(ld, st, buf + ll * LS, 1, t0, tws);
+    rgfft::run<T, true, M, 2, PL, rgfft::PAD_ROWS>(ld, st, buf + ll * LS, 1, t0, tws);
   } else {
     // p += s x: the last pass leaves x in shared memory; the update then runs
     // over consecutive cell pairs with four read-modify-writes in flight
-    rgfft::run<T, true, M, 2, false>(ld, [&](int e, cpx<T> v) { buf[ll * LS + rgfft::row(e)] = v; },
-                                     buf + ll * LS, 1, t0, tws);
+    rgfft::run<T, true, M, 2, PL, rgfft::PAD_ROWS>(ld, [&](int e, cpx<T> v) { buf[ll * LS + rgfft::row(e)] = v; },
+                                  buf + ll * LS, 1, t0, tws);
     __syncthreads();
     const uint32_t l0 = blockIdx.x * (uint32_t)L;
     constexpr int U = 4;
@@ -932,8 +1001,8 @@ int rg_xlines(int lpb) {
   const int lo = 32 / (M / 16) > 1 ? 32 / (M / 16) : 1, hi = 256 / (M / 16);
   return lpb < lo ? lo : (lpb > hi ? hi : lpb);
 }
-inline size_t xrg_smem(int nx, int L) {
-  return sizeof(cpx<float>) * ((size_t)xrg_stride(nx / 2) * L + (size_t)nx);
+inline size_t xrg_smem(int nx, int L, bool pl = false) {
+  return sizeof(cpx<float>) * ((size_t)(pl ? xrg_stride_pl(nx / 2) : xrg_stride(nx / 2)) * L + (size_t)nx);
 }
 
 template <typename T>
@@ -982,22 +1051,29 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
     cudaError_t e;
     if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
       // (the register-staged form reads f with 16-byte loads)
-      if (do_fft && (src != SRC_F || ((uintptr_t)in.f & 15u) == 0)) {
+      // (the plane layout has only these instances: f must be 16-byte aligned)
+      if (do_fft && (src != SRC_F || ((uintptr_t)in.f & 15u) == 0 || g.spec_planes)) {
         const int L = rg_xlines<N>(lpb);
         const int gr = (nlines + L - 1) / L;
-        const size_t smr = xrg_smem(g.nx, L);
+        const size_t smr = xrg_smem(g.nx, L, g.spec_planes != 0);
         auto go = [&](auto kernel) -> cudaError_t {
           cudaError_t e2 = allow_smem(kernel, smr);
           if (e2 != cudaSuccess) return e2;
           kernel<<<gr, L * (N / 16), smr, st>>>(g, in, sc, slot, fdf, pdf, (cpx<float>*)spec, (const cpx<float>*)tw, L);
           return cudaGetLastError();
         };
+        if (g.spec_planes) {
+          if (src == SRC_F) return go(k_xfwd_rg<SRC_F, N, false, true>);
+          if (src == SRC_FDF) return go(k_xfwd_rg<SRC_FDF, N, false, true>);
+          return go(k_xfwd_rg<SRC_RESID, N, false, true>);  // the plane layout has walls only
+        }
         if (src == SRC_F) return go(k_xfwd_rg<SRC_F, N, false>);
         if (src == SRC_FDF) return go(k_xfwd_rg<SRC_FDF, N, false>);
         if (!g.top_open) return go(k_xfwd_rg<SRC_RESID, N, false>);
         return go(k_xfwd_rg<SRC_RESID, N, true>);
       }
     }
+    if (g.spec_planes) return cudaErrorInvalidValue;  // plane layout: power-of-two nx/2 only
     if (src == SRC_F) {
       if ((e = allow_smem(k_xfwd<T, SRC_F, true, N>, sm)) != cudaSuccess) return e;
       k_xfwd<T, SRC_F, true, N><<<grid, 256, sm, st>>>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb);
@@ -1107,10 +1183,11 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
     cudaError_t e;
     // (the register-staged form writes an FP64 p with 16-byte stores)
     if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
-      if (mode != XI_F64 || ((uintptr_t)p & 15u) == 0) {
+      if (mode != XI_F64 || ((uintptr_t)p & 15u) == 0 || g.spec_planes) {
+      if (mode == XI_F64 && ((uintptr_t)p & 15u) != 0) return cudaErrorMisalignedAddress;
       const int L = rg_xlines<N>(lpb);
       const int gr = (nlines + L - 1) / L;
-      const size_t smr = xrg_smem(g.nx, L);
+      const size_t smr = xrg_smem(g.nx, L, g.spec_planes != 0);
       auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e2 = allow_smem(kernel, smr);
         if (e2 != cudaSuccess) return e2;
@@ -1118,11 +1195,17 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
                                                sc);
         return cudaGetLastError();
       };
+      if (g.spec_planes) {
+        if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N, true>);
+        if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N, true>);
+        return go(k_xinv_rg<XI_DF_ACC, N, true>);
+      }
       if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N>);
       if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N>);
       return go(k_xinv_rg<XI_DF_ACC, N>);
       }
     }
+    if (g.spec_planes) return cudaErrorInvalidValue;  // plane layout: power-of-two nx/2 only
     if (mode == XI_F64) {
       if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
       k_xinv<T, XI_F64, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);

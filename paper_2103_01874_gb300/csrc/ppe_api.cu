@@ -47,6 +47,14 @@ struct ppe_plan_s {
   df* wpre;           //   ... on z faces
   double2* rhs_part;  // per-CTA partial sums (2 ny nz entries: right-hand side, x transform; any tiling)
   DevScalars* sc;
+  // spectral schedule (ppe_tuning.spectral): FUSED (k_zyz.cu) where zyz_ok, PENCIL
+  // (k_pencil.cu) where pencil_ok; both keep the spectrum in the plane layout
+  // (gd.spec_planes), mapped by tmap (a fused pass's tile) and tmap_z (a z tile)
+  bool zyz_ok;
+  bool pencil_ok;
+  int sched;
+  alignas(64) CUtensorMap tmap;
+  alignas(64) CUtensorMap tmap_z;
   // refinement loops as CUDA graphs with a WHILE conditional node (FP32_REFINE):
   // ppe_solve's and ppe_project's (the latter ends with the fused correction)
   cudaGraphExec_t refine_exec;
@@ -271,16 +279,63 @@ int choose_tkx(int nz, bool fp32, bool zpass) {
 
 ppe_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPE_OK : PPE_ERR_CUDA; }
 
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime (no
+// link against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    fn = (EncodeTiledFn)f;
+  }
+  return fn;
+}
+
+// The spectrum in the plane layout as a 2-D tensor of 8-byte elements (one
+// complex FP32 value each): x = j (ny), y = kx nz + kz; a box is zyz_cols(ny, nz)
+// columns of j by nz rows of kz, i.e. one CTA's tile of one kx plane.  Row
+// pitch ny * 8 bytes (a multiple of 16 for every supported ny).
+bool make_spec_tmap(ppe_plan_t P, CUtensorMap* map, int box_cols) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const int ny = P->g.ny, nz = P->g.nz, nxh = P->nxh;
+  const cuuint64_t dims[2] = {(cuuint64_t)ny, (cuuint64_t)nz * (cuuint64_t)nxh};
+  const cuuint64_t strides[1] = {(cuuint64_t)ny * 8u};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)nz};
+  const cuuint32_t es[2] = {1u, 1u};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, P->spec, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool sched_ok(ppe_plan_t P, int s) {
+  return s == PPE_SPECTRAL_LEGACY || (s == PPE_SPECTRAL_FUSED && P->zyz_ok) ||
+         (s == PPE_SPECTRAL_PENCIL && P->pencil_ok);
+}
+
+void set_sched(ppe_plan_t P, int s) {
+  P->sched = sched_ok(P, s) ? s : PPE_SPECTRAL_LEGACY;
+  P->gd.spec_planes = P->sched != PPE_SPECTRAL_LEGACY ? 1 : 0;
+}
+
 // Kernel names reported by ppe_profile_read.
 enum KernelId { K_INIT, K_RHO_MIN, K_RHS, K_XFWD_F, K_XFWD_RESID, K_ZFFT_FWD, K_YTHOMAS, K_ZFFT_INV,
                 K_XINV, K_XINV_ACC, K_CORRECT, K_CHECK, K_DF_TO_D, K_VC_SETUP, K_VC_APPLY, K_VC_UPDATE,
-                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_DIV_S, K_CONST, K_COUNT };
+                K_VC_DOTS, K_VC_PUPDATE, K_VC_SCALAR, K_VC_CORRECT, K_DIV_S, K_CONST, K_ZYZ, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_init_scalars", "k_rho_min", "k_rhs_march", "k_xfwd_f",
                                            "k_xfwd_resid", "k_zfft_fwd", "k_ysolve", "k_zfft_inv",
                                            "k_xinv", "k_xinv_accum", "k_correct", "k_refine_check",
                                            "k_df_to_d", "k_vc_setup", "k_vc_apply", "k_vc_update",
                                            "k_vc_dots", "k_vc_pupdate", "k_vc_scalars", "k_vc_correct",
-                                           "k_div_constraint", "k_make_const"};
+                                           "k_div_constraint", "k_make_const", "k_zyz"};
 constexpr int kProfMax = 16384;
 
 int prof_begin(ppe_plan_t P, int id) {
@@ -358,6 +413,25 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   const double scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
   // the first pass after an x transform of f also totals the partial sums (finish_sums)
   DevScalars* fin = guarded ? nullptr : P->sc;
+  if (P->sched != PPE_SPECTRAL_LEGACY) {
+    const float* lam = (const float*)P->lam;
+    const cpx<float>* twz = (const cpx<float>*)P->tw_z;
+    const cpx<float>* twy = (const cpx<float>*)P->tw_y;
+    const cpx<float>* wqy = (const cpx<float>*)P->wq_y;
+    const float *lx = lam, *ly = lam + P->nxh, *lz = lam + P->nxh + P->g.ny;
+    if (P->sched == PPE_SPECTRAL_FUSED) {
+      PPE_LAUNCH(P, K_ZYZ, launch_zyz(P->gd, P->tmap, twz, twy, wqy, lx, ly, lz, P->sc, fin, P->stream));
+    } else {
+      PPE_LAUNCH(P, K_ZFFT_FWD, launch_zfft_tma(false, P->gd, P->tmap_z, twz, P->sc, fin, P->stream));
+      PPE_LAUNCH(P, K_YTHOMAS, launch_ydct_tma(P->gd, (cpx<float>*)P->spec, twy, wqy, lx, ly, lz, P->sc,
+                                               P->stream));
+      PPE_LAUNCH(P, K_ZFFT_INV, launch_zfft_tma(true, P->gd, P->tmap_z, twz, P->sc, nullptr, P->stream));
+    }
+    PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
+               launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
+                              P->stream));
+    return PPE_OK;
+  }
   PPE_LAUNCH(P, K_ZFFT_FWD,
              launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, fin, P->stream));
   if (P->fp32 && !P->gd.top_open) {  // DCT-II/III for walls; the open top uses the tridiagonal solve
@@ -784,6 +858,22 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       if (s == PPE_OK) s = cuda_status(set_smem_limits<double>());
     }
   }
+  // the plane-layout schedules where their kernels exist (and, for the fused
+  // pass, the GPU can co-schedule its clusters); LEGACY by default (measured
+  // fastest at 256^3 on a GB300: 1.126 ms per projection against 1.167 ms with
+  // PENCIL and 1.399 ms with FUSED), the others through ppe_set_tuning
+  {
+    const int M = g->nx / 2;
+    const bool base_ok = s == PPE_OK && P->fp32 && !P->gd.top_open && M >= 16 && M <= 512 && (M & (M - 1)) == 0;
+    if (base_ok && zyz_supported(g->ny, g->nz) && make_spec_tmap(P, &P->tmap, zyz_cols(g->ny, g->nz))) {
+      int nc = 0;
+      P->zyz_ok = zyz_max_clusters(P->gd, &nc) == cudaSuccess && nc > 0;
+      cudaGetLastError();
+    }
+    if (base_ok && pencil_supported(g->ny, g->nz))
+      P->pencil_ok = make_spec_tmap(P, &P->tmap_z, pencil_zcols(g->ny, g->nz));
+  }
+  set_sched(P, PPE_SPECTRAL_LEGACY);
   if (s == PPE_OK && P->fp32) s = build_refine_graphs(P);
   if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, 1.0, o.refine_tol, 0, P->stream));
   if (s == PPE_OK)
@@ -859,6 +949,7 @@ ppe_status ppe_get_tuning(ppe_plan_t P, ppe_tuning* t) {
   t->x_lines = P->lpb;
   t->z_cols = P->tkx;
   t->y_cols = P->tky;
+  t->spectral = P->sched;
   return PPE_OK;
 }
 
@@ -873,6 +964,7 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   if (t->rhs_planes < 1 || t->rhs_planes > nz) return PPE_ERR_INVALID_ARG;
   if (!pow2(t->x_lines, 1, 64)) return PPE_ERR_INVALID_ARG;
   if (!pow2(t->z_cols, 1, 16) || !pow2(t->y_cols, 1, 32)) return PPE_ERR_INVALID_ARG;
+  if (!sched_ok(P, t->spectral)) return PPE_ERR_INVALID_ARG;
   const size_t xs = P->fp32 ? (xfwd_smem<float>(nx, t->x_lines) > xinv_smem<float>(nx, t->x_lines)
                                    ? xfwd_smem<float>(nx, t->x_lines) : xinv_smem<float>(nx, t->x_lines))
                             : (xfwd_smem<double>(nx, t->x_lines) > xinv_smem<double>(nx, t->x_lines)
@@ -892,6 +984,7 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   P->lpb = t->x_lines;
   P->tkx = t->z_cols;
   P->tky = t->y_cols;
+  set_sched(P, t->spectral);
   if (P->fp32) return build_refine_graphs(P);
   return PPE_OK;
 }
@@ -1219,6 +1312,7 @@ namespace {
 // The report and status of one projection from a host copy of its scalars.
 ppe_status info_from(ppe_plan_t P, const DevScalars& h, ppe_info* info) {
   const double fmax = h.fmax_bits ? __builtin_bit_cast(double, h.fmax_bits) : 0.0;
+  const bool timed_out = h.dev_err != 0;  // a bounded wait for a bulk tensor copy ran out
   info->f_max = fmax;
   info->rho0 = __builtin_bit_cast(double, h.rho0_bits);
   bool incompatible = false;
@@ -1247,6 +1341,7 @@ ppe_status info_from(ppe_plan_t P, const DevScalars& h, ppe_info* info) {
       info->rel_residual = __builtin_bit_cast(double, h.rmax_bits[h.last_slot]) / fmax;
     else
       info->rel_residual = -1.0;
+    if (timed_out) return PPE_ERR_TIMEOUT;
     if (h.last_slot >= 0 && !h.done) return PPE_ERR_NOT_CONVERGED;
   } else {
     info->sweeps = 0;

@@ -1,5 +1,6 @@
 // Internal declarations shared by the libppe translation units.
 #pragma once
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -54,6 +55,8 @@ struct DevScalars {
   int f_ran;                                    // f_sum, f_mean belong to the current call
   int rhs_tiles, rhs_chunks;                    // tiling of the last k_rhs_march (0: none this call)
   int x_parts;                                  // CTAs of the last forward x transform of f (0: none)
+  int dev_err;                                  // device-side errors of the current call (bit 1: a bounded
+                                                // wait for a bulk tensor copy ran out); reported as PPE_ERR_TIMEOUT
   // unsplit projection (k_pcg.cu): conjugate-gradient state
   double pcg_alpha, pcg_beta, pcg_rz;           // step, direction update, r . z
   double pcg_gmean;                             // mean of the right side g (kept by r)
@@ -71,6 +74,8 @@ struct DevScalars {
 struct GridDev {
   int nx, ny, nz;
   int top_open;          // 1: outflow top (p = 0 on the face y = Ly, ghost p_ny = -p_{ny-1}); 0: wall
+  int spec_planes;       // spectrum layout: 0 [kz][j][kx] (kx fastest); 1 [kx][kz][j] (plane layout, the fused
+                         // z-y-z pass of k_zyz.cu; index kx * ny nz + line)
   double idx, idy, idz;  // 1/dx, 1/dy, 1/dz
   FastDiv fd_nx, fd_nxh, fd_m, fd_ny, fd_nyp1;  // dividers by nx, nx/2+1, nx/2, ny, ny+1
 };
@@ -168,6 +173,27 @@ size_t xpass_smem_limit();  // largest dynamic shared memory of the x passes (st
 template <typename T>
 size_t zpass_smem_limit();  // the same for the z pass
 
+// ---- fused z-y-z pass on the plane layout (k_zyz.cu) ----
+bool zyz_supported(int ny, int nz);  // ny, nz in {32, 64, 128, 256}
+int zyz_cols(int ny, int nz);        // j columns per CTA (the bulk tensor box width)
+// largest number of co-resident clusters of the kernel for this grid (0: cannot launch)
+cudaError_t zyz_max_clusters(const GridDev& g, int* n);
+// tmap: 2-D map of the spectrum {ny, nz (nx/2+1)}, 8-byte elements, box {zyz_cols, nz}.
+// err: dev_err of the calling plan; fin as in launch_zfft.
+cudaError_t launch_zyz(const GridDev& g, const CUtensorMap& tmap, const cpx<float>* tw_z, const cpx<float>* tw_y,
+                       const cpx<float>* wq, const float* lam_x, const float* lam_y, const float* lam_z,
+                       DevScalars* err, DevScalars* fin, cudaStream_t st);
+
+// ---- bulk-copy-staged z and y passes on the plane layout (k_pencil.cu) ----
+bool pencil_supported(int ny, int nz);  // ny, nz in {32, 64, 128, 256}
+int pencil_zcols(int ny, int nz);       // j columns of a z tile (the tensor map's box width)
+// tmap: 2-D map of the spectrum {ny, nz (nx/2+1)}, 8-byte elements, box {pencil_zcols(ny, nz), nz}
+cudaError_t launch_zfft_tma(bool inverse, const GridDev& g, const CUtensorMap& tmap, const cpx<float>* tw,
+                            DevScalars* err, DevScalars* fin, cudaStream_t st);
+cudaError_t launch_ydct_tma(const GridDev& g, cpx<float>* spec, const cpx<float>* tw, const cpx<float>* wq,
+                            const float* lam_x, const float* lam_y, const float* lam_z, DevScalars* err,
+                            cudaStream_t st);
+
 // ---- launchers (k_stencil.cu) ----
 // Eq. (31) divergence constraint (and the one-fluid density when rho != NULL)
 cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_g, const double* comp_l,
@@ -189,8 +215,6 @@ cudaError_t launch_correct_pre(const GridDev& g, double dt, const df* upre, cons
 cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const DevScalars* sc, double* u_out,
                                 double* v_out, double* w_out, cudaStream_t st);
 cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st);
-// Writes the per-call output pointers of ppe_project into sc (so that graphs
-// captured once can run with any outputs).
 // Eq. (33) from u_pre and p (pairs) fused with the residual r = f - L p of the
 // same p into rmax[iter + 1]; outputs through sc->out_*.
 cudaError_t launch_correct_check(const GridDev& g, const df* upre, const df* vpre, const df* wpre, const df* pdf,

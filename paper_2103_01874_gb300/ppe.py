@@ -24,6 +24,10 @@ FACE_ARITHMETIC = 0
 FACE_HARMONIC = 1
 BC_WALL = 0      # top boundary in y: wall (ppe_bc)
 BC_OUTFLOW = 1   # open top, p = 0 on the face
+# schedules of the spectral z and y steps (ppe_tuning.spectral)
+SPECTRAL_LEGACY = 0  # three passes, spectrum [kz][j][kx]
+SPECTRAL_FUSED = 1   # one cluster pass per kx plane
+SPECTRAL_PENCIL = 2  # three bulk-copy-staged persistent passes, spectrum [kx][kz][j]
 
 STATUS = {0: "PPE_OK", 1: "PPE_ERR_INVALID_ARG", 2: "PPE_ERR_UNSUPPORTED_SIZE", 3: "PPE_ERR_INCOMPATIBLE_RHS",
           4: "PPE_ERR_OUT_OF_MEMORY", 5: "PPE_ERR_NOT_CONVERGED", 6: "PPE_ERR_TIMEOUT", 7: "PPE_ERR_CUDA"}
@@ -52,7 +56,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("rhs_lines", c_int), ("rhs_planes", c_int), ("x_lines", c_int), ("z_cols", c_int),
-                ("y_cols", c_int)]
+                ("y_cols", c_int), ("spectral", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

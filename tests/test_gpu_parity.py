@@ -210,7 +210,7 @@ def test_tuning_does_not_change_results(precision, grid):
     with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=precision) as plan:
         for sh in shapes:
             plan.set_tuning(**sh)
-            assert plan.get_tuning() == sh
+            assert {k: plan.get_tuning()[k] for k in sh} == sh
             o = [torch.empty(fl.shape, dtype=torch.float64, device="cuda"), torch.empty_like(d["u"]),
                  torch.empty_like(d["v"]), torch.empty_like(d["w"])]
             plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, *o)
@@ -220,7 +220,7 @@ def test_tuning_does_not_change_results(precision, grid):
             plan.set_tuning(rhs_lines=3)
         with pytest.raises(ppe.PPEError):
             plan.set_tuning(rhs_planes=0)
-        assert plan.get_tuning() == shapes[-1]
+        assert {k: plan.get_tuning()[k] for k in shapes[-1]} == shapes[-1]
     for o in outs[1:]:
         for a, b in zip(o, outs[0]):
             assert np.array_equal(a, b)
