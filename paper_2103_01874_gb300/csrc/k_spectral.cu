@@ -573,7 +573,8 @@ __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const 
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
                                               const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
-                                              const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky) {
+                                              const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky,
+                                              const DevScalars* zsc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nxh = g.nx / 2 + 1, ny = g.ny;
   const int ntile = (nxh + tky - 1) / tky;
@@ -606,7 +607,11 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
     if (k == 0) {
       const T lam = lxz + lam_y[0];
       const cpx<T> v0 = V[c];
-      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n / lam;  // zero mode pinned
+      if (kx == 0 && kz == 0) {  // zero mode pinned (to the value that keeps p zero-mean)
+        V[c] = {(T)zsc->zmode, (T)0};
+        continue;
+      }
+      const T s = inv_n / lam;
       V[c] = {v0.x * s, v0.y * s};
       continue;
     }
@@ -642,7 +647,8 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
 template <typename T, int N>
 __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw,
                                                  const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
-                                                 const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L) {
+                                                 const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L,
+                                                 const DevScalars* zsc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
   const uint32_t ntile = (nxh + L - 1) / L;
@@ -675,7 +681,11 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
       const cpx<T> v0 = *Vk;
       // inv_n / lam as inv_n * (1/lam): inv_n is a power of two, so the correctly
       // rounded reciprocal times it is the correctly rounded quotient
-      const T s = (kx == 0 && kz == 0) ? (T)0 : inv_n * __frcp_rn(lam);  // zero mode pinned
+      if (kx == 0 && kz == 0) {  // zero mode pinned (to the value that keeps p zero-mean)
+        *Vk = {(T)zsc->zmode, (T)0};
+        continue;
+      }
+      const T s = inv_n * __frcp_rn(lam);
       *Vk = {v0.x * s, v0.y * s};
       continue;
     }
@@ -717,7 +727,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
 __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
                                                   const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
                                                   const float* __restrict__ lam_y, const float* __restrict__ lam_z,
-                                                  int L) {
+                                                  int L, const DevScalars* zsc) {
   using T = float;
   constexpr int N = 256;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -761,7 +771,11 @@ __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec,
     const int k = t0 + 16 * q;
     if (k == 0) {
       // inv_n / lam as inv_n * (1/lam): inv_n is a power of two
-      const T s0 = (kx == 0 && kz == 0) ? (T)0 : inv_n * __frcp_rn(lxz + lam_y[0]);
+      if (kx == 0 && kz == 0) {  // zero mode pinned (to the value that keeps p zero-mean)
+        v[0] = {(T)zsc->zmode, (T)0};
+        continue;
+      }
+      const T s0 = inv_n * __frcp_rn(lxz + lam_y[0]);
       v[0] = {v[0].x * s0, v[0].y * s0};
       continue;
     }
@@ -806,7 +820,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec,
 template <typename T, int MODE, int N>
 __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, df* pdf,
                                               double scale, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
-                                              const DevScalars* sc) {
+                                              const DevScalars* sc, DevScalars* psc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
@@ -842,6 +856,7 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
   __syncthreads();
   cpx<T>* z = fft_any<T, true, N, 2>(a, b, ilog2_dev(lpb), rp, lsc, 1, tws);
   const df sdf = d2df(scale);
+  df psum = {0.0f, 0.0f};  // sum of the p written (pairs)
   for (int idx = threadIdx.x; idx < lpb * M; idx += blockDim.x) {
     const int ll = (int)fdiv(idx, g.fd_m), n = idx - ll * M;
     const int line = l0 + ll;
@@ -855,12 +870,19 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
       const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
       if (MODE == XI_DF) {
         reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        psum = df_addz(df_addz(psum, d0), d1);
       } else {
         const float4 q = reinterpret_cast<const float4*>(pdf)[o >> 1];
         const df s0 = df_add(df{q.x, q.y}, d0), s1 = df_add(df{q.z, q.w}, d1);
         reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+        psum = df_addz(df_addz(psum, s0), s1);
       }
     }
+  }
+  if (MODE != XI_F64 && psc) {
+    // per-CTA sum of p, totalled in a fixed order by the next z pass (finish_sums)
+    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) psc->p_parts = (int)gridDim.x;
   }
 }
 
@@ -875,7 +897,7 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
 template <int MODE, int M, bool PL = false>
 __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
                                                  double scale, const cpx<float>* __restrict__ tw, int L,
-                                                 const DevScalars* sc) {
+                                                 const DevScalars* sc, DevScalars* psc) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
@@ -919,6 +941,7 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
   const cpx<T>* Xs = buf + ll * LS;
   const uint32_t c0 = line * (uint32_t)nx;
   const df sdf = d2df(scale);
+  df psum = {0.0f, 0.0f};  // sum of the p written (pairs)
   // Z_k = E_k + i O_k, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(W^k)/2
   auto ld = [&](int k) -> cpx<T> {
     if (!valid) return {(T)0, (T)0};
@@ -941,6 +964,7 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
       float4* q4 = reinterpret_cast<float4*>(pdf) + (o >> 1);
       if (MODE == XI_DF) {
         *q4 = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        psum = df_addz(df_addz(psum, d0), d1);
       } else {
         const float4 q = *q4;
         const df s0 = df_add(df{q.x, q.y}, d0), s1 = df_add(df{q.z, q.w}, d1);
@@ -976,8 +1000,14 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
         const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
         const df s0 = df_add(df{q[u].x, q[u].y}, d0), s1 = df_add(df{q[u].z, q[u].w}, d1);
         reinterpret_cast<float4*>(pdf)[(l0 + lq) * (uint32_t)M + n] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+        psum = df_addz(df_addz(psum, s0), s1);
       }
     }
+  }
+  if (MODE != XI_F64 && psc) {
+    // per-CTA sum of p, totalled in a fixed order by the next z pass (finish_sums)
+    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) psc->p_parts = (int)gridDim.x;
   }
 }
 
@@ -1142,7 +1172,8 @@ cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const i
 
 template <typename T>
 cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, const cpx<T>* wq,
-                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, cudaStream_t st) {
+                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, const DevScalars* zsc,
+                        cudaStream_t st) {
   const int nxh = g.nx / 2 + 1;
   const int grid = g.nz * ((nxh + tky - 1) / tky);
   const size_t sm = zfft_smem<T>(g.ny, tky);
@@ -1157,24 +1188,25 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
         if (e != cudaSuccess) return e;
         k_ydct256<<<gr, L * (N / 16), smr, st>>>(g, (cpx<float>*)spec, (const cpx<float>*)tw,
                                                  (const cpx<float>*)wq, (const float*)lam_x, (const float*)lam_y,
-                                                 (const float*)lam_z, L);
+                                                 (const float*)lam_z, L, zsc);
         return cudaGetLastError();
       }
       cudaError_t e = allow_smem(k_ydct_rg<T, N>, smr);
       if (e != cudaSuccess) return e;
-      k_ydct_rg<T, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, wq, lam_x, lam_y, lam_z, L);
+      k_ydct_rg<T, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc);
       return cudaGetLastError();
     }
     cudaError_t e = allow_smem(k_ydct<T, N>, sm);
     if (e != cudaSuccess) return e;
-    k_ydct<T, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky);
+    k_ydct<T, N><<<grid, 256, sm, st>>>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky, zsc);
     return cudaGetLastError();
   });
 }
 
 template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
-                        const RadixPlan& rp, const cpx<T>* tw, int lpb, const DevScalars* sc, cudaStream_t st) {
+                        const RadixPlan& rp, const cpx<T>* tw, int lpb, const DevScalars* sc, DevScalars* psc,
+                        cudaStream_t st) {
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
   const size_t sm = xinv_smem<T>(g.nx, lpb);
@@ -1192,7 +1224,7 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
         cudaError_t e2 = allow_smem(kernel, smr);
         if (e2 != cudaSuccess) return e2;
         kernel<<<gr, L * (N / 16), smr, st>>>(g, (const cpx<float>*)spec, p, pdf, scale, (const cpx<float>*)tw, L,
-                                               sc);
+                                               sc, psc);
         return cudaGetLastError();
       };
       if (g.spec_planes) {
@@ -1208,13 +1240,13 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
     if (g.spec_planes) return cudaErrorInvalidValue;  // plane layout: power-of-two nx/2 only
     if (mode == XI_F64) {
       if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
-      k_xinv<T, XI_F64, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+      k_xinv<T, XI_F64, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc, psc);
     } else if (mode == XI_DF) {
       if ((e = allow_smem(k_xinv<T, XI_DF, N>, sm)) != cudaSuccess) return e;
-      k_xinv<T, XI_DF, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+      k_xinv<T, XI_DF, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc, psc);
     } else {
       if ((e = allow_smem(k_xinv<T, XI_DF_ACC, N>, sm)) != cudaSuccess) return e;
-      k_xinv<T, XI_DF_ACC, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc);
+      k_xinv<T, XI_DF_ACC, N><<<grid, 256, sm, st>>>(g, spec, p, pdf, scale, rp, tw, lpb, sc, psc);
     }
     return cudaGetLastError();
   });
@@ -1234,9 +1266,10 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   template cudaError_t launch_ythomas<T>(const GridDev&, cpx<T>*, const T*, const int*, const int*, T,          \
                                          const DevScalars*, cudaStream_t);                                       \
   template cudaError_t launch_ydct<T>(const GridDev&, cpx<T>*, const RadixPlan&, const cpx<T>*, const cpx<T>*,     \
-                                      const T*, const T*, const T*, int, cudaStream_t);                          \
+                                      const T*, const T*, const T*, int, const DevScalars*, cudaStream_t);       \
   template cudaError_t launch_xinv<T>(int, const GridDev&, const cpx<T>*, double*, df*, double,                  \
-                                      const RadixPlan&, const cpx<T>*, int, const DevScalars*, cudaStream_t);
+                                      const RadixPlan&, const cpx<T>*, int, const DevScalars*, DevScalars*,      \
+                                      cudaStream_t);
 PPE_INST(double)
 PPE_INST(float)
 #undef PPE_INST

@@ -34,6 +34,8 @@ __global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep
   sc->f_ran = 0;
   sc->x_parts = 0;
   sc->dev_err = 0;
+  sc->zmode = 0.0;
+  sc->p_parts = 0;
   if (!keep_rho0) {  // a call that assembles f: its compatibility sums start here
     sc->smax_bits = 0ull;
     sc->wallv_bits = 0ull;

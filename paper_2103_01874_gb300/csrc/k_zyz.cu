@@ -147,7 +147,11 @@ __global__ void __launch_bounds__(ZyzCfg<NY, NZ>::THREADS, 1)
       if (k == 0) {
         const cpx<T> v0 = V[0];
         // inv_n / lam as inv_n * (1/lam): inv_n is a power of two
-        const T s = (kx == 0 && kzr == 0) ? (T)0 : inv_n * __frcp_rn(lxz + ly[0]);
+        if (kx == 0 && kzr == 0) {  // zero mode pinned (to the value that keeps p zero-mean)
+          V[0] = {(T)err->zmode, (T)0};
+          continue;
+        }
+        const T s = inv_n * __frcp_rn(lxz + ly[0]);
         V[0] = {v0.x * s, v0.y * s};
         continue;
       }

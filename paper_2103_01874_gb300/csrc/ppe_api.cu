@@ -45,7 +45,7 @@ struct ppe_plan_s {
   df* upre;           // explicitly split velocity u_pre on x faces (ppe_project)
   df* vpre;           //   ... on y faces
   df* wpre;           //   ... on z faces
-  double2* rhs_part;  // per-CTA partial sums (2 ny nz entries: right-hand side, x transform; any tiling)
+  double2* rhs_part;  // per-CTA partial sums (3 ny nz entries: right-hand side, forward and inverse x transforms)
   DevScalars* sc;
   // spectral schedule (ppe_tuning.spectral): FUSED (k_zyz.cu) where zyz_ok, PENCIL
   // (k_pencil.cu) where pencil_ok; both keep the spectrum in the plane layout
@@ -405,9 +405,12 @@ StencilIn make_in(ppe_plan_t P, const double* u, const double* v, const double* 
 }
 
 // z forward, y solve, z inverse, x inverse (mode XI_F64: p64 = x; XI_DF:
-// pdf = x; XI_DF_ACC: pdf += x)
+// pdf = x; XI_DF_ACC: pdf += x).  psum: the x inverse also sums the p it writes,
+// and the next solve's zero mode takes minus that sum (the refinement keeps p
+// zero-mean); off where the solve is a preconditioner, not a pressure.
 template <typename T>
-ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded) {
+ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded, bool psum = true) {
+  DevScalars* psc = (psum && mode != XI_F64) ? P->sc : nullptr;
   const DevScalars* sc = guarded ? P->sc : nullptr;
   cpx<T>* spec = (cpx<T>*)P->spec;
   const double scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
@@ -429,7 +432,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
     }
     PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
                launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
-                              P->stream));
+                              psc, P->stream));
     return PPE_OK;
   }
   PPE_LAUNCH(P, K_ZFFT_FWD,
@@ -437,7 +440,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   if (P->fp32 && !P->gd.top_open) {  // DCT-II/III for walls; the open top uses the tridiagonal solve
     const T* lam = (const T*)P->lam;
     PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
-                                            lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->stream));
+                                            lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->sc, P->stream));
   } else {
     PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas<T>(P->gd, spec, (const T*)P->tab, P->line_off, P->line_len, (T)P->a_y,
                                                sc, P->stream));
@@ -446,7 +449,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
              launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, nullptr, P->stream));
   PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
              launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
-                            P->stream));
+                            psc, P->stream));
   return PPE_OK;
 }
 
@@ -623,11 +626,11 @@ ppe_status vc_precond(ppe_plan_t P) {
   if (P->fp32) {
     PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<float>*)P->spec,
                                                P->rp_half, (const cpx<float>*)P->tw_x, P->lpb, P->stream));
-    return solve_tail<float>(P, XI_DF, nullptr, zs, false);
+    return solve_tail<float>(P, XI_DF, nullptr, zs, false, false);
   }
   PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<double>*)P->spec,
                                               P->rp_half, (const cpx<double>*)P->tw_x, P->lpb, P->stream));
-  return solve_tail<double>(P, XI_DF, nullptr, zs, false);
+  return solve_tail<double>(P, XI_DF, nullptr, zs, false, false);
 }
 
 // One iteration: Kp, alpha, x and r, z = M^{-1} r, beta and the test, p.
@@ -767,7 +770,7 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   b += (fp32 ? 16 : 8) * n;                                             // f (and p) as pairs
   b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
-  b += 32 * (size_t)g->ny * g->nz;                                       // per-CTA partial sums
+  b += 48 * (size_t)g->ny * g->nz;                                       // per-CTA partial sums
   return b;
 }
 
@@ -840,10 +843,10 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
-  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, 2 * sizeof(double2) * g->ny * g->nz));
+  if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, 3 * sizeof(double2) * g->ny * g->nz));
   P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 : 1) * sizeof(df) * ncell +
                  sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz) +
-                 2 * sizeof(double2) * g->ny * g->nz;
+                 3 * sizeof(double2) * g->ny * g->nz;
   choose_rhs_tiles(P);
   if (s == PPE_OK) {
     if (P->fp32) {

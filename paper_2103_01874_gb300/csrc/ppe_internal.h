@@ -55,6 +55,12 @@ struct DevScalars {
   int f_ran;                                    // f_sum, f_mean belong to the current call
   int rhs_tiles, rhs_chunks;                    // tiling of the last k_rhs_march (0: none this call)
   int x_parts;                                  // CTAs of the last forward x transform of f (0: none)
+  // mean of p kept at zero by the refinement: the inverse x transform that forms
+  // p writes per-CTA partial sums (p_parts of them, part[2 ny nz ..]); the next
+  // first z pass totals them into zmode = -sum(p) / ny, the zero-mode value of
+  // the next correction's spectrum (so p + correction has zero mean)
+  double zmode;
+  int p_parts;
   int dev_err;                                  // device-side errors of the current call (bit 1: a bounded
                                                 // wait for a bulk tensor copy ran out); reported as PPE_ERR_TIMEOUT
   // unsplit projection (k_pcg.cu): conjugate-gradient state
@@ -66,9 +72,10 @@ struct DevScalars {
   double pcg_tol;
   unsigned long long pcg_gmax_bits, pcg_rmax_bits;
   int pcg_iter, pcg_max, pcg_cont;
-  double2* part;                                // per-CTA partial sums, plan workspace (2 ny nz entries):
+  double2* part;                                // per-CTA partial sums, plan workspace (3 ny nz entries):
                                                 //   [0, ny nz): k_rhs_march (wall flux, wall tiles only)
                                                 //   [ny nz, 2 ny nz): forward x transform (sum of f)
+                                                //   [2 ny nz, 3 ny nz): inverse x transform (sum of p)
 };
 
 struct GridDev {
@@ -150,16 +157,19 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
 template <typename T>
 cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const RadixPlan& rp,
                         const cpx<T>* tw_z, int tkx, const DevScalars* sc, DevScalars* fin, cudaStream_t st);
+// y passes of the FP32 solve: zsc->zmode is the value given to the zero mode
 template <typename T>
 cudaError_t launch_ythomas(const GridDev& g, cpx<T>* spec, const T* tab, const int* line_off,
                            const int* line_len, T a, const DevScalars* sc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, const cpx<T>* wq,
-                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, cudaStream_t st);
+                        const T* lam_x, const T* lam_y, const T* lam_z, int tky, const DevScalars* zsc,
+                        cudaStream_t st);
+// psc non-NULL (XI_DF, XI_DF_ACC): the per-CTA sums of the p written go to psc->part[2 ny nz ..]
 template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp_half, const cpx<T>* tw_x, int lpb, const DevScalars* sc,
-                        cudaStream_t st);
+                        DevScalars* psc, cudaStream_t st);
 template <typename T>
 size_t xfwd_smem(int nx, int lpb);
 template <typename T>
@@ -179,7 +189,7 @@ int zyz_cols(int ny, int nz);        // j columns per CTA (the bulk tensor box w
 // largest number of co-resident clusters of the kernel for this grid (0: cannot launch)
 cudaError_t zyz_max_clusters(const GridDev& g, int* n);
 // tmap: 2-D map of the spectrum {ny, nz (nx/2+1)}, 8-byte elements, box {zyz_cols, nz}.
-// err: dev_err of the calling plan; fin as in launch_zfft.
+// err: dev_err of the calling plan (and zmode, the zero mode's value); fin as in launch_zfft.
 cudaError_t launch_zyz(const GridDev& g, const CUtensorMap& tmap, const cpx<float>* tw_z, const cpx<float>* tw_y,
                        const cpx<float>* wq, const float* lam_x, const float* lam_y, const float* lam_z,
                        DevScalars* err, DevScalars* fin, cudaStream_t st);
@@ -192,7 +202,7 @@ cudaError_t launch_zfft_tma(bool inverse, const GridDev& g, const CUtensorMap& t
                             DevScalars* err, DevScalars* fin, cudaStream_t st);
 cudaError_t launch_ydct_tma(const GridDev& g, cpx<float>* spec, const cpx<float>* tw, const cpx<float>* wq,
                             const float* lam_x, const float* lam_y, const float* lam_z, DevScalars* err,
-                            cudaStream_t st);
+                            cudaStream_t st);  // err->zmode: the zero mode's value
 
 // ---- launchers (k_stencil.cu) ----
 // Eq. (31) divergence constraint (and the one-fluid density when rho != NULL)

@@ -189,9 +189,19 @@ __device__ __forceinline__ void sum_parts_fixed(const double2* part, int n, doub
 __device__ __forceinline__ void finish_sums(DevScalars* sc, const GridDev& g) {
   const size_t nynz = (size_t)g.ny * g.nz;
   const int xp = sc->x_parts;
-  double fs = 0.0, unused;
+  const int pp = sc->p_parts;
+  double fs = 0.0, ps = 0.0, unused;
   if (xp > 0) sum_parts_fixed(sc->part + nynz, xp, &fs, &unused);
+  __syncthreads();  // thread 0 has read the first reduction's shared scratch
+  // the sum of the p the last inverse x transform formed: the next correction's
+  // zero mode is -sum(p)/ny, which adds -mean(p) to p after the inverse transforms
+  // (DCT-III unscaled in its zero mode, z and x inverses scaled by 1/(nx nz))
+  if (pp > 0) sum_parts_fixed(sc->part + 2 * nynz, pp, &ps, &unused);
   if (threadIdx.x != 0) return;
+  if (pp > 0) {
+    sc->zmode = -ps / (double)g.ny;
+    sc->p_parts = 0;
+  }
   const int nt = sc->rhs_tiles, nc = sc->rhs_chunks;
   if (nt > 0) {
     double ws = 0.0;

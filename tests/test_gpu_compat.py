@@ -81,7 +81,7 @@ def test_incompatible_is_reported_and_the_compatible_part_solved(precision):
     fmax = np.abs(ref["f"]).max()
     assert abs(info.f_mean_removed - ref["f"].mean()) <= 1e-12 * fmax
     assert abs(info.f_mean_removed) > 1e-5 * fmax  # far above the 1e-12 test
-    tol = 1e-12 if precision == ppe.FP64 else 1e-8
+    tol = 1e-12 if precision == ppe.FP64 else 1e-11
     for k in ("p", "u", "v", "w"):
         assert O.rel_linf(res[k], ref[k]) <= tol, k
     if precision == ppe.FP32_REFINE:
@@ -134,7 +134,7 @@ def test_fp32_solve_of_f_with_a_mean_converges():
         assert e.value.code == 3
         info = plan.info(allow_incompatible=True)
     assert 0 <= info.rel_residual <= 1e-10
-    assert O.rel_linf(p.cpu().numpy(), phi) < 1e-8
+    assert O.rel_linf(p.cpu().numpy(), phi) < 1e-11
     assert abs(info.f_mean_removed - (7.0 + (lam * phi).mean())) <= 1e-13 * abs(lam)
     assert math.isnan(info.s_mean)  # no right-hand side was assembled by this plan
 

@@ -20,13 +20,16 @@ def test_limits_match_the_oracle(shape, precision):
     assert ppe.size_supported(*shape)
     fl = fields.make_fields(*shape, seed=51, recipe="single", width=2.0)
     ref = O.project_fields(fl)
-    res, info = project_gpu(fl, precision=precision)
-    tol = 1e-12 if precision == ppe.FP64 else 1e-8
+    # 1024-point lines make L's condition number ~1e5; the field error of the
+    # refinement form is about that times its stopping residual, so these grids
+    # refine to 1e-12 (one more sweep where the first stops above it)
+    res, info = project_gpu(fl, precision=precision, refine_tol=1e-12)
+    tol = 1e-12 if precision == ppe.FP64 else 1e-11
     for k in ("p", "u", "v", "w", "f"):
         err = np.abs(res[k] - ref[k]).max() / np.abs(ref[k]).max()
         assert err <= tol, (k, err)
     if precision == ppe.FP32_REFINE:
-        assert info.rel_residual <= 1e-10
+        assert info.rel_residual <= 1e-12
 
 
 def test_one_past_the_limits_is_refused():

@@ -2,7 +2,8 @@
 
 Bars: FP64 path rel L-inf <= 1e-12 on f, p, u, v, w; FP32 solve + FP64
 refinement: rel residual ||f - L p||_inf / ||f||_inf <= 1e-10 (checked on the
-host in FP64 from the returned f and p), p, u, v, w reported against the oracle.
+host in FP64 from the returned f and p), and p, u, v, w within 1e-11 of the
+oracle (one sweep measures ~3e-13), p zero-mean like the oracle's.
 """
 import math
 
@@ -16,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL_RES = 1e-10
+TOL_REF = 1e-11   # FP32 solve + refinement, fields against the oracle
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -113,7 +115,8 @@ def test_project_fp32_refine(shape):
     assert info.rel_residual <= TOL_RES
     assert O.rel_linf(res["f"], ref["f"]) <= TOL64
     for k in ("p", "u", "v", "w"):
-        assert O.rel_linf(res[k], ref[k]) <= 1e-8, k
+        assert O.rel_linf(res[k], ref[k]) <= TOL_REF, k
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
 
 
 def test_project_128_fp64_full():
@@ -134,7 +137,35 @@ def test_project_256_fp32_refine_full():
     assert rel <= TOL_RES, rel
     assert O.rel_linf(res["f"], ref["f"]) <= TOL64
     for k in ("p", "u", "v", "w"):
-        assert O.rel_linf(res[k], ref[k]) <= 1e-8, k
+        assert O.rel_linf(res[k], ref[k]) <= TOL_REF, k
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
+
+
+def test_project_256_fp64_full():
+    """The 256^3, 640/60 workload in the plain FP64 form, whole-field comparison."""
+    fl = fields.multimode_256()
+    ref = O.project_fields(fl)
+    res, _ = project_gpu(fl)
+    _compare(fl, res, ref, TOL64)
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
+
+
+@pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
+def test_project_384x256x384_full(precision):
+    """The largest served grid, 384 x 256 x 384 (nx = 384 takes the general
+    right-hand-side kernel and radix-3 x transforms), multimode 640/60, whole
+    fields against the oracle."""
+    fl = fields.make_fields(384, 256, 384, seed=19, recipe="multimode", width=6.0, rho_g=60.0)
+    ref = O.project_fields(fl)
+    res, info = project_gpu(fl, precision=precision)
+    if precision == ppe.FP64:
+        _compare(fl, res, ref, TOL64)
+    else:
+        assert info.rel_residual <= TOL_RES
+        assert O.rel_linf(res["f"], ref["f"]) <= TOL64
+        for k in ("p", "u", "v", "w"):
+            assert O.rel_linf(res[k], ref[k]) <= TOL_REF, k
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
 
 
 def test_project_host_buffers():

@@ -76,10 +76,9 @@ def test_schedule_matches_oracle(grid, sched):
     assert info.rel_residual <= TOL_RES
     assert _host_residual(fl, res["f"], res["p"]) <= TOL_RES
     assert O.rel_linf(res["f"], ref["f"]) <= 1e-12
-    for k in ("u", "v", "w"):
+    for k in ("p", "u", "v", "w"):
         assert O.rel_linf(res[k], ref[k]) <= TOL_FIELD, k
-    pm = res["p"] - res["p"].mean()
-    assert O.rel_linf(pm, ref["p"]) <= TOL_FIELD
+    assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
 
 
 @pytest.mark.parametrize("grid", [(64, 64, 64), (32, 128, 256)])
@@ -101,8 +100,8 @@ def test_schedules_agree(grid):
         for other in res[1:]:
             for k in ("p", "u", "v", "w"):
                 a, b = res[0][k], other[k]
-                if k == "p":
-                    a, b = a - a.mean(), b - b.mean()
+                if k == "p" and not sweeps:
+                    a, b = a - a.mean(), b - b.mean()  # the FP32 solve alone keeps a mean at its rounding
                 assert O.rel_linf(a, b) <= tol, (sweeps, k, O.rel_linf(a, b))
 
 
