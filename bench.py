@@ -14,8 +14,9 @@ Prints ONE JSON line (rank 0).  For N > 1 every rank runs an independent replica
 of the workload on its own GPU (no collective on the data path); value is the
 total solves of all ranks over the slowest rank's time.
 
---impl reference times the FP64 CPU oracle (the reference arm: a plain
-numpy/scipy restatement of the paper's method) on this host.
+--impl reference times the FP64 CPU oracle (the reference arm: a plain,
+single-threaded C++ restatement of the paper's method with its own FFT and
+Thomas solver) on this host.
 """
 from __future__ import annotations
 
@@ -623,25 +624,30 @@ def run_served(args, dev):
 # ---------------------------------------------------------------------------
 # CPU oracle (the reference arm / cpu_baseline)
 # ---------------------------------------------------------------------------
+# The oracle timed: the C++ FP64 projection (oracle/ppe_oracle.cpp, g++ -O3,
+# one thread), on the bench's 256^3 fields.
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
-from oracle import ppe_oracle as O
+from oracle import cpp
 from paper_2103_01874_gb300 import fields
+cpp.lib()
 fl = fields.multimode_256()
 times = []
 for s in range({n}):
     t = time.perf_counter()
-    O.project_fields(fl)
+    cpp.project_fields(fl)
     times.append(time.perf_counter() - t)
 print(json.dumps(times))
 """
 
-
-REF_MAX_SOLVES = 30
+ORACLE_KIND = "oracle (C++ FP64, own mixed-radix FFT and Thomas y solve, g++ -O3, 1 thread)"
+REF_MAX_SOLVES = 3  # about 20 s each on one core
 
 
 def oracle_times(n: int):
+    from oracle import cpp
+    cpp.build()  # compiled once here, before the timed processes start
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=n)], capture_output=True,
@@ -653,31 +659,30 @@ def oracle_times(n: int):
 
 def oracle_all_cores():
     """Secondary CPU figure: one oracle process per host core, all started at
-    once; each times a second whole 256^3 solve after an untimed first one, and
-    the throughput is the sum of the per-process rates (about 3 GB of host
-    memory per process)."""
+    once; each times one whole 256^3 solve, and the throughput is the sum of the
+    per-process rates (about 2 GB of host memory per process)."""
     k = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    procs = [subprocess.Popen([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=2)], stdout=subprocess.PIPE,
+    procs = [subprocess.Popen([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=1)], stdout=subprocess.PIPE,
                               stderr=subprocess.PIPE, text=True, env=env) for _ in range(k)]
     rates = []
     for pr in procs:
         out, err = pr.communicate(timeout=1800)
         if pr.returncode != 0:
             raise RuntimeError(err[-2000:])
-        rates.append(1.0 / json.loads(out.strip().splitlines()[-1])[1])
-    return {"value": sum(rates), "unit": "solves/s", "cores": k, "kind": "oracle",
-            "sample": f"{k} concurrent processes (one per host core, 1 thread each), one timed 256^3 solve each "
-                      f"after an untimed one; per-process {min(rates):.3f}-{max(rates):.3f} solves/s"}
+        rates.append(1.0 / json.loads(out.strip().splitlines()[-1])[0])
+    return {"value": sum(rates), "unit": "solves/s", "cores": k, "kind": ORACLE_KIND,
+            "sample": f"{k} concurrent processes (one per host core, 1 thread each), one timed 256^3 solve each; "
+                      f"per-process {min(rates):.3f}-{max(rates):.3f} solves/s"}
 
 
 def cpu_baseline(args):
     n = max(1, args.cpu_solves)
     times = oracle_times(n)
-    return {"value": n / sum(times), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} whole 256^3 projections (FP64 numpy/scipy oracle, 1 thread), "
-                      f"{sum(times):.1f} s of CPU work; best {min(times):.2f} s/solve",
+    return {"value": n / sum(times), "unit": "solves/s", "cores": 1, "kind": ORACLE_KIND,
+            "sample": f"{n} whole 256^3 projection(s), {sum(times):.1f} s of CPU work on one core; "
+                      f"best {min(times):.2f} s/solve",
             "all_cores": oracle_all_cores()}
 
 
@@ -686,11 +691,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return None
-    # bounded sample: one untimed solve (imports, FFT plans), then at most
-    # REF_MAX_SOLVES timed whole 256^3 solves (about 1.6 s each on one core)
+    # bounded sample: at most REF_MAX_SOLVES timed whole 256^3 solves (about
+    # 20 s each on one core; the oracle is compiled before the timed process)
     n_timed = max(1, min(args.steps, REF_MAX_SOLVES))
-    times = oracle_times(1 + n_timed)
-    timed = times[1:]
+    timed = oracle_times(n_timed)
     total = sum(timed)
     value = len(timed) / total
     return {
@@ -709,10 +713,9 @@ def run_reference(args):
         "data": "synthetic (seeded two-phase fields, numpy default_rng)",
         "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "precision": "fp64 (oracle)",
                    "parallelism": "single host core"},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": ORACLE_KIND,
                          "sample": f"{len(timed)} whole 256^3 projections timed (of {args.steps} steps asked; "
-                                   f"capped at {REF_MAX_SOLVES} so the run ends in about a minute), "
-                                   f"1 untimed solve first"},
+                                   f"capped at {REF_MAX_SOLVES} so the run ends in about a minute)"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -724,7 +727,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--max-sweeps", type=int, default=8)
-    ap.add_argument("--cpu-solves", type=int, default=3)
+    ap.add_argument("--cpu-solves", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=256, help="grid edge (profiling runs only; the bench line is 256)")
     ap.add_argument("--forms", default="fp32,fp64", help="fp32 (always) and/or fp64")

@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import cpp
 from oracle import ppe_oracle as O
 from paper_2103_01874_gb300 import fields, ppe
 
@@ -51,8 +52,22 @@ def test_project_fp64(shape, recipe, width, lengths):
     ref = O.project_fields(fl)
     res, info = project_gpu(fl)
     _compare(fl, res, ref, TOL64)
+    _compare(fl, res, cpp.project_fields(fl), TOL64)  # the C++ oracle (own FFT and Thomas) too
     assert info.rho0 == ref["rho0"]
     assert abs(res["p"].mean()) <= 1e-13 * np.abs(res["p"]).max()
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 24, 36), (18, 27, 54)])
+@pytest.mark.parametrize("rule", [ppe.FACE_ARITHMETIC, ppe.FACE_HARMONIC])
+def test_project_fp32_refine_vs_cpp_oracle(shape, rule):
+    """The refinement form against the C++ oracle, both face rules."""
+    fl = fields.make_fields(*shape, seed=sum(shape), recipe="multimode", width=4.0, rho_g=60.0)
+    ref = cpp.project_fields(fl, rule=rule)
+    res, info = project_gpu(fl, precision=ppe.FP32_REFINE, face_rule=rule)
+    assert info.rel_residual <= TOL_RES
+    assert O.rel_linf(res["f"], ref["f"]) <= TOL64
+    for k in ("p", "u", "v", "w"):
+        assert O.rel_linf(res[k], ref[k]) <= TOL_REF, k
 
 
 @pytest.mark.parametrize("rule", [ppe.FACE_ARITHMETIC, ppe.FACE_HARMONIC])
@@ -120,11 +135,12 @@ def test_project_fp32_refine(shape):
 
 
 def test_project_128_fp64_full():
-    """The 128^3 multimode workload, whole-field comparison."""
+    """The 128^3 multimode workload, whole-field comparison with both oracles."""
     fl = fields.multimode_128()
     ref = O.project_fields(fl)
     res, _ = project_gpu(fl)
     _compare(fl, res, ref, TOL64)
+    _compare(fl, res, cpp.project_fields(fl), TOL64)
 
 
 def test_project_256_fp32_refine_full():
