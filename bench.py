@@ -537,7 +537,7 @@ def run_batched(args, dev):
     a loop of plain FP64 projections of the same grids, one after another."""
     import torch
 
-    from paper_2103_01874_gb300 import fields, ppe
+    from paper_2103_01874_gb300 import autotune, fields, ppe
     shapes = fields.batch_shapes(64, seed=3)
     items64, items32 = [], []
     for n, (nx, ny, nz) in enumerate(shapes):
@@ -549,18 +549,28 @@ def run_batched(args, dev):
                      v_out=torch.empty_like(d["v"]), w_out=torch.empty_like(d["w"]), dt=fl.dt)
             items.append((plan, o))
     stream = torch.cuda.current_stream(dev)
-    batch = ppe.Batch(items32, stream=stream)
-    for _ in range(2):
-        batch.launch()
-    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
-    e0.record(stream)
-    for _ in range(reps):
-        batch.launch()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_batch = e0.elapsed_time(e1) / reps
+
+    def time_batch():
+        batch = ppe.Batch(items32, stream=stream)
+        for _ in range(2):
+            batch.launch()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            batch.launch()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        batch.close()
+        return e0.elapsed_time(e1) / reps
+
+    ms_default = time_batch()
+    # autotuned: each distinct grid tuned once (spectral schedule by the whole
+    # projection's time, then the x-line tile), the others of its size class
+    # take the cached result; the batch graph is then captured again
+    tuned = tune_plans(items32, {k: autotune.SEARCH[k] for k in ("spectral", "x_lines")}, stream)
+    ms_batch = time_batch()
     worst = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
 
     def loop64():
@@ -577,48 +587,104 @@ def run_batched(args, dev):
     torch.cuda.synchronize(dev)
     ms_loop = e0.elapsed_time(e1) / reps
     pts = sum(a * b * c for a, b, c in shapes)
-    batch.close()
     for pl, _ in items32 + items64:
         pl.close()
     return {"workload": "64 uneven grids (dims from {32,48,64,96,128,192}), FP32 solve + FP64 refinement to 1e-10, "
-                        "one CUDA graph launch",
+                        "one CUDA graph launch, autotuned plans",
             "solves_per_s": 64 / (ms_batch * 1e-3), "ms_per_batch": ms_batch, "gpts_per_s": pts / (ms_batch * 1e-3) / 1e9,
             "max_rel_residual": worst, "cells": pts,
+            "untuned": {"solves_per_s": 64 / (ms_default * 1e-3), "ms_per_batch": ms_default},
+            "autotune": tuned,
             "fp64_loop": {"solves_per_s": 64 / (ms_loop * 1e-3), "ms_per_batch": ms_loop}}
 
 
+def tune_plans(items, search, stream, path=None):
+    """Autotune each (plan, fields) item, once per size class: the first plan of
+    a class is searched on its own fields, the others take the cached tuning.
+    Returns how often each spectral schedule was chosen and the tuning time."""
+    import tempfile
+
+    from paper_2103_01874_gb300 import autotune
+    path = path or os.path.join(tempfile.mkdtemp(prefix="ppe_tune_"), "tuning.json")
+    t0 = time.perf_counter()
+    chosen = {}
+    for plan, o in items:
+        plan.set_stream(stream)
+        if not autotune.apply_cached(plan, path):
+            def run(k, plan=plan, o=o):
+                for _ in range(k):
+                    plan.project(o["u"], o["v"], o["w"], o["S"], o["rho"], o["p_n"], o["p_nm1"], o["dt"], o["p"],
+                                 o["u_out"], o["v_out"], o["w_out"])
+            autotune.autotune(plan, run, reps=2, path=path, search=search)
+        name = {0: "legacy", 1: "fused", 2: "pencil"}[plan.get_tuning()["spectral"]]
+        chosen[name] = chosen.get(name, 0) + 1
+    return {"search": list(search), "schedules_chosen": chosen, "seconds": time.perf_counter() - t0,
+            "cache": path}
+
+
 def run_served(args, dev):
-    """Poisson arrivals (mean 200 req/s) of grids from 64^3 to 384x256x384, half
-    FP64 and half FP32 + refinement, admitted under a 150 GB budget."""
-    from paper_2103_01874_gb300 import ppe, serve
+    """Poisson arrivals (mean 200 req/s) of grids from 64^3 to 384x256x384,
+    admitted under a 150 GB budget: the mixed stream (half FP64, half FP32 +
+    refinement) and, on the same arrival trace, an all-FP64 stream.  Every
+    request projects its own seeded fields (request seed s uses resident set
+    s mod 4 of its shape, drawn before the clock starts)."""
+    from paper_2103_01874_gb300 import autotune, ppe, serve
     shapes = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 192, 192), (256, 256, 256), (384, 256, 384)]
     probs = [0.3, 0.2, 0.2, 0.15, 0.1, 0.05]
-    reqs = serve.poisson_requests(args.served_requests, rate=200.0, shapes=shapes, probs=probs, seed=11,
-                                  fp64=ppe.FP64, fp32=ppe.FP32_REFINE)
-    ex = serve.CudaExecutor(slots=8, device=dev.index)
-    for s in set(r.shape for r in reqs):
-        ex.template(s)  # resident input templates, generated before the clock starts
+    import tempfile
+
+    import torch
+    pool = 4
+    cache = os.path.join(tempfile.mkdtemp(prefix="ppe_tune_"), "tuning.json")
+    ex = serve.CudaExecutor(slots=8, device=dev.index, pool=pool, autotune_cache=cache)
+    ex.prepare(shapes)   # the seeded input sets, resident before the clock starts
     ex.prealloc(shapes)  # per-slot field buffers
+    # every size class tuned before the clock (the executor applies the cache to
+    # each plan it creates)
+    tune_items = []
+    for shp in shapes:
+        dd, fl = ex.fields_of(shp, 0)
+        for prec in (ppe.FP64, ppe.FP32_REFINE):
+            plan = ppe.Plan(*shp, fl.lx, fl.ly, fl.lz, precision=prec, refine_tol=1e-10, max_sweeps=8)
+            o = dict(dd, p=torch.empty_like(dd["rho"]), u_out=torch.empty_like(dd["u"]),
+                     v_out=torch.empty_like(dd["v"]), w_out=torch.empty_like(dd["w"]), dt=fl.dt)
+            tune_items.append((plan, o))
+    tuned = tune_plans(tune_items, autotune.SEARCH, torch.cuda.current_stream(dev), path=cache)
+    for plan, _ in tune_items:
+        plan.close()
+    del tune_items
     srv = serve.Server(ex, budget_bytes=150 << 30, slots=8)
+
+    def stream(seed, fp32_share):
+        return serve.poisson_requests(args.served_requests, rate=200.0, shapes=shapes, probs=probs, seed=seed,
+                                      fp32_share=fp32_share, fp64=ppe.FP64, fp32=ppe.FP32_REFINE)
+
     # steady state: an untimed replay of an arrival trace of the same law (other
     # seed) lets the plan pool grow to what concurrent requests of each size class
     # need, as a long-running server would have it resident
-    warm = serve.poisson_requests(args.served_requests, rate=200.0, shapes=shapes, probs=probs, seed=12,
-                                  fp64=ppe.FP64, fp32=ppe.FP32_REFINE)
+    warm = stream(12, 0.5)
     for r in warm:
         r.rid = -1 - r.rid
     srv.run(warm)
     # and a resident pool of at least 3 plans per size class and precision
     srv.reserve([(s, p) for s in shapes for p in (ppe.FP64, ppe.FP32_REFINE)], per_class=3)
     created_warm = srv.plans_created
-    stats, _ = srv.run(reqs)
+    out = {}
+    for name, share in (("mixed", 0.5), ("fp64_only", 0.0)):
+        reqs = stream(11, share)  # the same arrival times and shapes; only the precisions differ
+        before = srv.plans_created
+        stats, _ = srv.run(reqs)
+        worst = max((r.rel_residual for r in reqs if r.precision == ppe.FP32_REFINE), default=float("nan"))
+        d = stats.as_dict()
+        d.update(requests=len(reqs), fp32_requests=sum(r.precision == ppe.FP32_REFINE for r in reqs),
+                 max_rel_residual_fp32=worst, plans_created=srv.plans_created - before)
+        out[name] = d
     srv.close()
-    worst = max((r.rel_residual for r in reqs if r.precision == ppe.FP32_REFINE), default=float("nan"))
-    out = stats.as_dict()
-    out.update(workload="Poisson 200 req/s, grids 64^3..384x256x384, 50% FP64 / 50% FP32+refine, 150 GB budget, "
-                        "8 slots", requests=len(reqs), max_rel_residual_fp32=worst,
-               plans_created_in_warmup=created_warm, plans_created=stats.plans_created - created_warm)
-    return out
+    res = dict(out["mixed"])
+    res.update(workload="Poisson 200 req/s, grids 64^3..384x256x384, 50% FP64 / 50% FP32+refine, 150 GB budget, "
+                        "8 slots; per-request seeded fields (4 resident sets per shape)",
+               plans_created_in_warmup=created_warm, fp64_only=out["fp64_only"], autotune=tuned)
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -721,6 +787,8 @@ def run_reference(args):
 
 
 def main():
+    import faulthandler
+    faulthandler.enable()  # a fatal signal prints the Python stack of every thread
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)  # ~0.45 s timed: several clock samples

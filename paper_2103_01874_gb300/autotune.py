@@ -1,13 +1,20 @@
-"""Launch-shape autotuner for libppe plans.
+"""Schedule and launch-shape autotuner for libppe plans.
 
-A plan's tile sizes (ppe_set_tuning: lines per CTA of the right-hand-side
-kernel and of the x transforms, columns per CTA of the z and y passes, planes
-per marching chunk) change no result bit, only speed.  `autotune` times the
-candidate shapes on the caller's own fields with the plan's per-kernel CUDA
-events (ppe_profile), coordinate by coordinate -- each shape only moves the
-time of its own kernel -- applies the best, and remembers it in a JSON cache
-keyed by grid, precision, face rule and GPU name, so that later plans of the
-same size class start from the tuned shapes (`apply_cached`).
+ppe_set_tuning exposes two kinds of choices:
+  * the spectral schedule of the solve (LEGACY three passes on the
+    [kz][j][kx] spectrum, FUSED cluster pass per kx plane, PENCIL bulk-copy-
+    staged passes on the [kx][kz][j] spectrum), which changes which kernels
+    run, so it is scored by the whole projection's device time (the sum of the
+    per-kernel CUDA-event times of ppe_profile);
+  * tile sizes (lines per CTA of the right-hand-side kernel and of the x
+    transforms, columns per CTA of the z and y passes, planes per marching
+    chunk), which change no result bit and only the time of their own kernel,
+    so each is scored by that kernel alone.
+`autotune` searches them coordinate by coordinate on the caller's own fields
+(the schedule first, since it decides which kernels the tile sizes drive),
+applies the best and remembers it in a JSON cache keyed by grid, precision,
+face rule and GPU name, so that later plans of the same size class start from
+it (`apply_cached`).
 """
 from __future__ import annotations
 
@@ -19,8 +26,12 @@ from . import ppe
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ppe_gb300", "tuning.json")
 
-# which kernel each field of ppe_tuning drives, and the values tried
+STEP = "step"  # score: the sum of all kernel times of the projection
+
+# which kernel each field of ppe_tuning drives, and the values tried (in this
+# order: the schedule decides which kernels the later fields drive)
 SEARCH = {
+    "spectral": (STEP, (0, 1, 2)),
     "rhs_lines": ("k_rhs_march", (1, 2, 4, 8)),
     "rhs_planes": ("k_rhs_march", (4, 8, 16, 32)),
     "x_lines": ("k_xinv", (4, 8, 16, 32, 64)),
@@ -79,6 +90,8 @@ def _kernel_us(plan, run, kernel: str, reps: int) -> float:
     run(reps)
     kt = plan.profile_read()
     plan.profile(False)
+    if kernel == STEP:
+        return 1e3 * sum(ms for _, ms in kt.values()) / reps if kt else float("inf")
     if kernel not in kt:
         return float("inf")
     launches, ms = kt[kernel]
@@ -102,7 +115,9 @@ def autotune(plan: "ppe.Plan", run, reps: int = 3, path: str | None = DEFAULT_CA
             try:
                 plan.set_tuning(**trial)
             except ppe.PPEError:
-                continue  # shape out of range or too much shared memory for this grid
+                continue  # out of range, too much shared memory, or a schedule this plan lacks
+            if kernel == STEP:
+                run(1)  # first use of a schedule (graph rebuild, first launches)
             scores.append((_kernel_us(plan, run, kernel, reps), v))
         if scores:
             t, v = min(scores)

@@ -1015,10 +1015,12 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
 // launchers
 // ---------------------------------------------------------------------------
 // Lines per CTA of the register-staged passes: the tuned tile, raised so that a
-// CTA (L * N/16 threads) holds at least one full warp.
+// CTA (L * N/16 threads) holds at least one full warp and capped so that it
+// holds at most 256 threads (the kernels' launch bound).
 template <int N>
 int rg_lines(int tile) {
-  return tile > 32 / (N / 16) ? tile : 32 / (N / 16);
+  constexpr int lo = 32 / (N / 16) > 1 ? 32 / (N / 16) : 1, hi = 256 / (N / 16);
+  return tile < lo ? lo : (tile > hi ? hi : tile);
 }
 template <typename T>
 size_t rg_smem(int n, int L) {

@@ -569,7 +569,12 @@ ppe_status build_refine_graph(ppe_plan_t P, int mode, cudaGraphExec_t* exec) {
   ppe_status st = capture_refine(P, mode);
   P->stream = saved;
   cudaGraph_t outg = nullptr;
-  if (cudaStreamEndCapture(cs, &outg) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+  if (cudaStreamEndCapture(cs, &outg) != cudaSuccess) {
+    // an invalidated capture leaves the graph to the runtime: it is not
+    // destroyed here (a second destroy of a released graph crashes the process)
+    g = nullptr;
+    if (st == PPE_OK) st = PPE_ERR_CUDA;
+  }
   if (st != PPE_OK) return fail(st);
   if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) return fail(PPE_ERR_CUDA);
   cudaGraphDestroy(g);
@@ -982,14 +987,20 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
     cudaGraphExecDestroy(P->pcg_exec);
     P->pcg_exec = nullptr;
   }
-  P->tj = t->rhs_lines;
-  P->kc = t->rhs_planes;
-  P->lpb = t->x_lines;
-  P->tkx = t->z_cols;
-  P->tky = t->y_cols;
-  set_sched(P, t->spectral);
-  if (P->fp32) return build_refine_graphs(P);
-  return PPE_OK;
+  ppe_tuning prev;
+  ppe_get_tuning(P, &prev);
+  auto apply = [&](const ppe_tuning& u) {
+    P->tj = u.rhs_lines;
+    P->kc = u.rhs_planes;
+    P->lpb = u.x_lines;
+    P->tkx = u.z_cols;
+    P->tky = u.y_cols;
+    set_sched(P, u.spectral);
+    return P->fp32 ? build_refine_graphs(P) : PPE_OK;
+  };
+  const ppe_status s = apply(*t);
+  if (s != PPE_OK) apply(prev);  // the plan keeps its previous shapes and graphs
+  return s;
 }
 
 ppe_status ppe_profile(ppe_plan_t P, int enable) {

@@ -214,14 +214,20 @@ class Server:
 
 
 class CudaExecutor:
-    """libppe on one GPU: slot streams, resident per-shape input templates,
-    ppe_project on the slot's stream, completion events.  Each slot keeps one
-    set of field buffers (seven inputs, four outputs) per shape it has served,
-    so that a request copies its inputs device to device instead of allocating
-    (an allocation can synchronise the whole device); `prealloc` creates them
-    up front."""
+    """libppe on one GPU: slot streams, ppe_project on the slot's stream,
+    completion events.
 
-    def __init__(self, slots: int = 8, device=None, templates=None, autotune_cache=None):
+    Inputs: every request projects its own seeded fields (the single-interface
+    recipe of fields.make_fields).  Generating a large grid's fields on the host
+    takes seconds, so they are drawn ahead of the traffic into a resident pool
+    of `pool` distinct seeded sets per shape: request seed s uses set s mod pool
+    (field seed field_seed(shape, s mod pool)).  Each slot keeps one set of
+    field buffers (seven inputs, four outputs) per shape it has served, and a
+    request copies its set into them device to device instead of allocating (an
+    allocation can synchronise the whole device); `prealloc` creates the
+    buffers and `prepare` the pool up front."""
+
+    def __init__(self, slots: int = 8, device=None, pool: int = 4, inputs=None, autotune_cache=None):
         import torch
 
         from . import fields as F
@@ -229,15 +235,40 @@ class CudaExecutor:
         self.torch, self.ppe, self.F = torch, ppe, F
         self.dev = torch.device("cuda", device if device is not None else torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
-        self.templates = templates if templates is not None else {}
+        self.pool = max(1, int(pool))
+        self.inputs = inputs if inputs is not None else {}  # (shape, k) -> (device arrays, host Fields)
         self.autotune_cache = autotune_cache
         self.buffers = {}  # (slot, shape) -> (inputs, outputs)
+
+    @staticmethod
+    def field_seed(shape, k):
+        """Seed of pool set k of a shape (distinct across shapes and sets)."""
+        nx, ny, nz = shape
+        return 100003 * k + 7 * nx + 3 * ny + nz
+
+    def fields_of(self, shape, seed):
+        """(device arrays, host Fields) of the set a request with this seed projects."""
+        k = int(seed) % self.pool
+        t = self.inputs.get((shape, k))
+        if t is None:
+            nx, ny, nz = shape
+            fl = self.F.make_fields(nx, ny, nz, seed=self.field_seed(shape, k), recipe="single", width=2.0)
+            t = ({n: self.torch.from_numpy(v).to(self.dev) for n, v in fl.arrays().items()}, fl)
+            self.inputs[(shape, k)] = t
+        return t
+
+    def prepare(self, shapes):
+        """Draw every pool set of these shapes (before the clock starts)."""
+        for shape in shapes:
+            for k in range(self.pool):
+                self.fields_of(shape, k)
+        self.torch.cuda.synchronize(self.dev)
 
     def _bufs(self, slot, shape):
         b = self.buffers.get((slot, shape))
         if b is None:
             torch = self.torch
-            tmpl, _ = self.template(shape)
+            tmpl, _ = self.fields_of(shape, 0)
             with torch.cuda.stream(self.streams[slot]):
                 d = {k: torch.empty_like(v) for k, v in tmpl.items()}
                 out = dict(p=torch.empty_like(d["rho"]), u=torch.empty_like(d["u"]), v=torch.empty_like(d["v"]),
@@ -250,15 +281,6 @@ class CudaExecutor:
             for shape in shapes:
                 self._bufs(slot, shape)
         self.torch.cuda.synchronize(self.dev)
-
-    def template(self, shape):
-        t = self.templates.get(shape)
-        if t is None:
-            nx, ny, nz = shape
-            fl = self.F.make_fields(nx, ny, nz, seed=nx * 7 + ny * 3 + nz, recipe="single", width=2.0)
-            t = ({k: self.torch.from_numpy(v).to(self.dev) for k, v in fl.arrays().items()}, fl)
-            self.templates[shape] = t
-        return t
 
     def field_bytes(self, shape):
         nx, ny, nz = shape
@@ -276,7 +298,7 @@ class CudaExecutor:
 
     def create_plan(self, shape, precision):
         nx, ny, nz = shape
-        _, fl = self.template(shape)
+        _, fl = self.fields_of(shape, 0)  # the box lengths (the same for every set of a shape)
         plan = self.ppe.Plan(nx, ny, nz, fl.lx, fl.ly, fl.lz, precision=precision, refine_tol=1e-10, max_sweeps=8,
                              stream=self.streams[0])
         if self.autotune_cache:
@@ -290,10 +312,10 @@ class CudaExecutor:
     def launch(self, req, plan, slot):
         torch = self.torch
         s = self.streams[slot]
-        tmpl, fl = self.template(req.shape)
+        src, fl = self.fields_of(req.shape, req.seed)
         d, out = self._bufs(slot, req.shape)
         with torch.cuda.stream(s):
-            for k, v in tmpl.items():  # this request's fields, in the slot's buffers
+            for k, v in src.items():  # this request's fields, in the slot's buffers
                 d[k].copy_(v, non_blocking=True)
         plan.set_stream(s)
         plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, out["p"], out["u"],

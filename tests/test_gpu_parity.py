@@ -273,6 +273,34 @@ def test_tuning_does_not_change_results(precision, grid):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("spectral", [ppe.SPECTRAL_LEGACY, ppe.SPECTRAL_PENCIL])
+def test_largest_tiles_on_long_lines(spectral):
+    """The largest tile values on 256- and 512-point lines (the y pass with 32
+    columns, the z pass with 16, the x passes with 64 lines) are capped inside
+    the launchers at 256 threads per CTA and give the same bits as the default
+    shapes; every value ppe_set_tuning accepts launches."""
+    import torch
+    fl = fields.make_fields(32, 256, 512 if spectral == ppe.SPECTRAL_LEGACY else 256, seed=23, recipe="multimode",
+                            width=4.0)
+    d = dev_fields(fl)
+    outs = []
+    with ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE) as plan:
+        plan.set_tuning(spectral=spectral)
+        for sh in (None, dict(rhs_lines=8, rhs_planes=32, x_lines=64, z_cols=16, y_cols=32),
+                   dict(rhs_lines=1, rhs_planes=1, x_lines=1, z_cols=1, y_cols=1)):
+            if sh:
+                plan.set_tuning(**sh)
+            o = [torch.empty(fl.shape, dtype=torch.float64, device="cuda"), torch.empty_like(d["u"]),
+                 torch.empty_like(d["v"]), torch.empty_like(d["w"])]
+            plan.project(d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], fl.dt, *o)
+            torch.cuda.synchronize()
+            outs.append([t.cpu().numpy() for t in o])
+            assert plan.info().rel_residual <= TOL_RES
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", [ppe.FP64, ppe.FP32_REFINE])
 def test_views_at_an_odd_double_offset(precision):
     """Device arrays that start 8 bytes past a 16-byte boundary (views into a
