@@ -71,7 +71,10 @@ typedef enum {
  * in double-float pairs (two FP32 numbers carrying about 48 significant bits,
  * relative rounding ~2^-48 = 3.6e-15 per operation), because FP64 issues at
  * about 1/64 of the FP32 rate on this GPU.
- * PPE_FP64: the transforms and the tridiagonal y solve in native FP64.
+ * PPE_FP64: with walls and every dimension <= 512, the transforms and the
+ * y solve (a cosine transform) in the same pairs, on the FP32 pipe; otherwise
+ * (an outflow top, or 1024-point lines, where pair rounding would exceed 1e-12
+ * of the result) the transforms and a tridiagonal y solve in native FP64.
  * PPE_FP32_REFINE: the transforms and the y solve in FP32 inside an iterative
  * refinement whose residual and update are formed in the pairs above. */
 typedef enum { PPE_FP64 = 0, PPE_FP32_REFINE = 1 } ppe_precision;

@@ -253,4 +253,32 @@ PPE_HD double df2d_alu(df a) {
   return d_from((uint64_t)((int64_t)Hb + (int64_t)k));
 }
 
+// ---------------------------------------------------------------------------
+// dd: a double-float number with arithmetic operators, so that templates
+// written for float and double (the FFT passes, the cosine-transform y solve)
+// run in pair arithmetic.  Each operator is the normalised pair operation
+// above (relative error about 2^-47 per operation).  Construction from a
+// double splits it into the nearest float and the float of the remainder
+// (exact to 2^-48 relative; used for compile-time constants and host tables --
+// device code converts FP64 data with d2df, which needs no FP64 instruction).
+// ---------------------------------------------------------------------------
+struct alignas(8) dd {
+  float hi, lo;
+  dd() = default;
+  PPE_HD constexpr dd(float h, float l) : hi(h), lo(l) {}
+  PPE_HD constexpr dd(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  PPE_HD constexpr dd(int x) : hi((float)x), lo(0.0f) {}  // exact for |x| < 2^24
+  PPE_HD constexpr dd(df a) : hi(a.hi), lo(a.lo) {}
+  PPE_HD explicit operator double() const { return (double)hi + (double)lo; }
+  PPE_HD df pair() const { return {hi, lo}; }
+};
+PPE_HD dd operator+(dd a, dd b) { return dd(df_add(a.pair(), b.pair())); }
+PPE_HD dd operator-(dd a, dd b) { return dd(df_sub(a.pair(), b.pair())); }
+PPE_HD dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+PPE_HD dd operator*(dd a, dd b) { return dd(df_mul(a.pair(), b.pair())); }
+PPE_HD dd operator/(dd a, dd b) { return dd(df_mul(a.pair(), df_recip(b.pair()))); }
+PPE_HD dd& operator+=(dd& a, dd b) { return a = a + b; }
+PPE_HD dd& operator-=(dd& a, dd b) { return a = a - b; }
+PPE_HD dd& operator*=(dd& a, dd b) { return a = a * b; }
+
 }  // namespace ppe

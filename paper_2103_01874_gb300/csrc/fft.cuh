@@ -75,7 +75,7 @@ __device__ __forceinline__ cpx<T> tw16(cpx<T> v) {
   if (m == 8) return {-v.x, -v.y};
   if (m == 4) return rot<T, INV>(v);                 // -i forward
   if (m == 12) return rot<T, !INV>(v);               // +i forward
-  const T cr = (T)c, si = INV ? (T)s : (T)(-s);      // w = c - i s (forward)
+  constexpr T cr = (T)c, si = INV ? (T)s : (T)(-s);  // w = c - i s (forward)
   return {v.x * cr - v.y * si, v.x * si + v.y * cr};
 }
 
@@ -92,9 +92,10 @@ template <typename T, bool INV> struct SmallDft<T, INV, 2> {
 template <typename T, bool INV> struct SmallDft<T, INV, 3> {
   // y1 = v0 - (v1+v2)/2 -+ i (sqrt(3)/2)(v1 - v2), y2 = conjugate rotation
   static __device__ __forceinline__ void run(cpx<T>* v) {
-    const T s3 = (T)0.86602540378443864676372317075294;
+    constexpr T s3 = (T)0.86602540378443864676372317075294;
     cpx<T> t1 = cadd(v[1], v[2]);
-    cpx<T> t2 = {v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y};
+    constexpr T half = (T)0.5;
+    cpx<T> t2 = {v[0].x - half * t1.x, v[0].y - half * t1.y};
     cpx<T> d = csub(v[1], v[2]);
     cpx<T> t3 = {s3 * d.x, s3 * d.y};
     v[0] = cadd(v[0], t1);

@@ -26,6 +26,7 @@ struct ppe_plan_s {
   int lpb;            // lines per CTA in the x passes
   int tkx;            // kx columns per CTA in the z pass
   bool fp32;
+  bool pairs;         // PPE_FP64 with walls: transforms and y solve in double-float pairs (dd)
   size_t cplx_bytes;
   void* spec;         // cpx<T>[nz][ny][nxh]
   void* tw_x;         // cpx<T>[nx]: exp(-2 pi i t/nx)
@@ -437,7 +438,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   }
   PPE_LAUNCH(P, K_ZFFT_FWD,
              launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, fin, P->stream));
-  if (P->fp32 && !P->gd.top_open) {  // DCT-II/III for walls; the open top uses the tridiagonal solve
+  if ((P->fp32 || P->pairs) && !P->gd.top_open) {  // DCT-II/III for walls; the open top: tridiagonal solve
     const T* lam = (const T*)P->lam;
     PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
                                             lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->sc, P->stream));
@@ -451,6 +452,14 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
              launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
                             psc, P->stream));
   return PPE_OK;
+}
+
+// Runs f(T{}) with T the element type of a PPE_FP64 plan's spectral passes:
+// double-float pairs with walls, native FP64 with an outflow top.
+template <typename F>
+ppe_status with_fp64_type(ppe_plan_t P, F&& f) {
+  if (P->pairs) return f(dd(0));
+  return f(0.0);
 }
 
 // Refinement sequences of PPE_FP32_REFINE (after the first FP32 solve left p
@@ -633,9 +642,12 @@ ppe_status vc_precond(ppe_plan_t P) {
                                                P->rp_half, (const cpx<float>*)P->tw_x, P->lpb, P->stream));
     return solve_tail<float>(P, XI_DF, nullptr, zs, false, false);
   }
-  PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<double>*)P->spec,
-                                              P->rp_half, (const cpx<double>*)P->tw_x, P->lpb, P->stream));
-  return solve_tail<double>(P, XI_DF, nullptr, zs, false, false);
+  return with_fp64_type(P, [&](auto tag) -> ppe_status {
+    using T = decltype(tag);
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<T>(SRC_FDF, true, P->gd, in, P->sc, 0, r, nullptr, (cpx<T>*)P->spec,
+                                           P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, P->stream));
+    return solve_tail<T>(P, XI_DF, nullptr, zs, false, false);
+  });
 }
 
 // One iteration: Kp, alpha, x and r, z = M^{-1} r, beta and the test, p.
@@ -814,6 +826,10 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   P->opt = o;
   P->stream = (cudaStream_t)stream;
   P->fp32 = o.precision == PPE_FP32_REFINE;
+  // pairs round at 2^-48 per operation: lines of up to 512 points keep the
+  // fields within 1e-12 of FP64 results; longer lines (and the outflow top's
+  // tridiagonal solve) stay in native FP64
+  P->pairs = !P->fp32 && o.bc_top == PPE_BC_WALL && g->nx <= 512 && g->ny <= 512 && g->nz <= 512;
   P->nxh = g->nx / 2 + 1;
   P->gd.nx = g->nx;
   P->gd.ny = g->ny;
@@ -859,6 +875,11 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       if (s == PPE_OK) s = make_twiddles<float>(&P->tw_z, g->nz);
       if (s == PPE_OK) s = P->gd.top_open ? make_thomas<float>(P) : make_dct_tables<float>(P);
       if (s == PPE_OK) s = cuda_status(set_smem_limits<float>());
+    } else if (P->pairs) {
+      s = make_twiddles<dd>(&P->tw_x, g->nx);
+      if (s == PPE_OK) s = make_twiddles<dd>(&P->tw_z, g->nz);
+      if (s == PPE_OK) s = make_dct_tables<dd>(P);
+      if (s == PPE_OK) s = cuda_status(set_smem_limits<dd>());
     } else {
       s = make_twiddles<double>(&P->tw_x, g->nx);
       if (s == PPE_OK) s = make_twiddles<double>(&P->tw_z, g->nz);
@@ -978,7 +999,7 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
                             : (xfwd_smem<double>(nx, t->x_lines) > xinv_smem<double>(nx, t->x_lines)
                                    ? xfwd_smem<double>(nx, t->x_lines) : xinv_smem<double>(nx, t->x_lines));
   const size_t zs = P->fp32 ? zfft_smem<float>(nz, t->z_cols) : zfft_smem<double>(nz, t->z_cols);
-  const size_t ys = P->fp32 ? zfft_smem<float>(ny, t->y_cols) : 0;
+  const size_t ys = P->fp32 ? zfft_smem<float>(ny, t->y_cols) : (P->pairs ? zfft_smem<dd>(ny, t->y_cols) : 0);
   const size_t xlim = P->fp32 ? xpass_smem_limit<float>() : xpass_smem_limit<double>();
   const size_t zlim = P->fp32 ? zpass_smem_limit<float>() : zpass_smem_limit<double>();
   if (xs > xlim || zs > zlim || ys > lim) return PPE_ERR_INVALID_ARG;
@@ -1067,10 +1088,12 @@ ppe_status ppe_solve(ppe_plan_t P, const double* f, double* p) {
                launch_df_to_d(P->pdf, p, (size_t)P->g.nx * P->g.ny * P->g.nz, P->stream));
     return PPE_OK;
   }
-  PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_F, true, P->gd, in, P->sc, 0, nullptr, nullptr,
-                                              (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->lpb,
-                                              P->stream));
-  return solve_tail<double>(P, XI_F64, p, nullptr, false);
+  return with_fp64_type(P, [&](auto tag) -> ppe_status {
+    using T = decltype(tag);
+    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<T>(SRC_F, true, P->gd, in, P->sc, 0, nullptr, nullptr, (cpx<T>*)P->spec,
+                                           P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, P->stream));
+    return solve_tail<T>(P, XI_F64, p, nullptr, false);
+  });
 }
 
 ppe_status ppe_correct(ppe_plan_t P, const double* u, const double* v, const double* w, const double* rho,
@@ -1111,10 +1134,13 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
   } else {
     PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre, P->tj, P->kc,
                                     P->stream));
-    PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<double>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr,
-                                                (cpx<double>*)P->spec, P->rp_half, (const cpx<double>*)P->tw_x, P->lpb,
-                                                P->stream));
-    if ((s = solve_tail<double>(P, XI_F64, F->p, nullptr, false)) != PPE_OK) return s;
+    s = with_fp64_type(P, [&](auto tag) -> ppe_status {
+      using T = decltype(tag);
+      PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<T>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr, (cpx<T>*)P->spec,
+                                             P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, P->stream));
+      return solve_tail<T>(P, XI_F64, F->p, nullptr, false);
+    });
+    if (s != PPE_OK) return s;
     PPE_LAUNCH(P, K_CORRECT, launch_correct_pre(P->gd, F->dt, P->upre, P->vpre, P->wpre, nullptr, F->p, P->sc,
                                                 F->u_out, F->v_out, F->w_out, P->stream));
   }

@@ -1,5 +1,9 @@
 // Spectral kernels of the direct Poisson solve of Eq. (34) (the fast Poisson
 // solver stated after Eq. (34): periodic x and z, homogeneous Neumann walls in y).
+// Templates on the element type T, instantiated for FP32 (k_spectral_f32.cu,
+// with the register-staged forms), FP64 (k_spectral_f64.cu) and double-float
+// pairs dd (k_spectral_dd.cu), one translation unit each so that they build in
+// parallel.
 //
 // Spectrum layout (plan workspace): complex T, [kz][j][kx] with kx fastest,
 // kx = 0 .. nx/2 (nxh = nx/2 + 1 values, the real-input half spectrum), j the
@@ -16,6 +20,7 @@
 //   k_xinv    one CTA per `lpb` lines: half spectrum -> real line, scaled, and
 //             stored to p (FP64), stored as pairs, or added to the pairs
 //             (refinement update).
+#pragma once
 #include <type_traits>
 
 #include "async.cuh"
@@ -115,7 +120,9 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         const size_t c = (size_t)l0 * nx + idx;
         const double x = __ldg(in.f + c);
         const df v = d2df(x);
-        if (sizeof(T) == 8) {
+        if constexpr (std::is_same<T, dd>::value) {
+          val = T(v);
+        } else if constexpr (sizeof(T) == 8) {
           val = (T)x;
         } else {
           if (fdf) fdf[c] = v;
@@ -143,7 +150,8 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
         const int idx = b0 + u * blockDim.x + threadIdx.x;
         if (idx >= lpb * nx) continue;
         const int ll = (int)fdiv(idx, g.fd_nx);
-        line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d_alu(v[u]) : (T)df_to_f(v[u]);
+        if constexpr (std::is_same<T, dd>::value) line_re[idx + ll * 2] = T(v[u]);
+        else line_re[idx + ll * 2] = (sizeof(T) == 8) ? (T)df2d_alu(v[u]) : (T)df_to_f(v[u]);
         fsum = df_addz(fsum, v[u]);
       }
     }
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
           const df ly = df_subz(df_addz(pyp[u], pym[u]), p2);
           const df lap = df_addz(df_addz(df_mulz(lx, lc[0]), df_mulz(ly, lc[1])), df_mulz(lz, lc[2]));
           const float r = df_to_f(df_subz(df_subz(fv[u], fmean), lap));
-          val = (T)r;
+          val = T(r);
           vmax = fmaxf(vmax, fabsf(r));
         }
         line_re[idx + (int)fdiv(idx, g.fd_nx) * 2] = val;
@@ -724,7 +732,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
 // Each thread forms V'_k for its own k with the operations k_ydct_rg uses for
 // that member of the pair (k, N-k) (the compiler may contract products into
 // sums differently, so the last bits can differ; the FP32 solve is refined).
-__global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
+static __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
                                                   const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
                                                   const float* __restrict__ lam_y, const float* __restrict__ lam_z,
                                                   int L, const DevScalars* zsc) {
@@ -863,7 +871,22 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
     if (line >= nlines) continue;
     const cpx<T> v = z[ll * lsc + n];
     const size_t o = (size_t)line * nx + 2 * n;
-    if (MODE == XI_F64) {
+    if constexpr (std::is_same<T, dd>::value) {
+      // pairs: scaled in pair arithmetic, written as FP64 or pairs
+      const df d0 = df_mul(sdf, v.x.pair()), d1 = df_mul(sdf, v.y.pair());
+      if (MODE == XI_F64) {
+        p[o] = df2d(d0);
+        p[o + 1] = df2d(d1);
+      } else if (MODE == XI_DF) {
+        reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        psum = df_addz(df_addz(psum, d0), d1);
+      } else {
+        const float4 q = reinterpret_cast<const float4*>(pdf)[o >> 1];
+        const df s0 = df_add(df{q.x, q.y}, d0), s1 = df_add(df{q.z, q.w}, d1);
+        reinterpret_cast<float4*>(pdf)[o >> 1] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+        psum = df_addz(df_addz(psum, s0), s1);
+      }
+    } else if (MODE == XI_F64) {
       p[o] = scale * (double)v.x;
       p[o + 1] = scale * (double)v.y;
     } else {
@@ -1272,8 +1295,6 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
   template cudaError_t launch_xinv<T>(int, const GridDev&, const cpx<T>*, double*, df*, double,                  \
                                       const RadixPlan&, const cpx<T>*, int, const DevScalars*, DevScalars*,      \
                                       cudaStream_t);
-PPE_INST(double)
-PPE_INST(float)
-#undef PPE_INST
+
 
 }  // namespace ppe
