@@ -52,9 +52,22 @@ __device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int nl_log2, co
 
 // Calls f(std::integral_constant<int, N>) with N = n for the lengths that have
 // compile-time instances (FP32 only), N = 0 otherwise.
+// reciprocal for the eigenvalue divide: the correctly rounded float reciprocal,
+// or the pair reciprocal
+template <typename T>
+__device__ __forceinline__ T rcp_of(T x) {
+  if constexpr (std::is_same<T, dd>::value) return dd(df_recip(x.pair()));
+  else return __frcp_rn(x);
+}
+
+// FP32 and pair passes have compile-time-length instances (register-staged
+// for powers of two); FP64 passes run on run-time radix plans
+template <typename T>
+struct has_ct_lengths : std::integral_constant<bool, sizeof(T) == 4 || std::is_same<T, dd>::value> {};
+
 template <typename T, typename F>
 cudaError_t with_len(int n, F&& f) {
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (has_ct_lengths<T>::value) {
     switch (n) {
       case 16: return f(std::integral_constant<int, 16>{});
       case 24: return f(std::integral_constant<int, 24>{});
@@ -693,7 +706,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
         *Vk = {(T)zsc->zmode, (T)0};
         continue;
       }
-      const T s = inv_n * __frcp_rn(lam);
+      const T s = inv_n * rcp_of(lam);
       *Vk = {v0.x * s, v0.y * s};
       continue;
     }
@@ -706,7 +719,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
     const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
     const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
     const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
-    const T sk = inv_n * __frcp_rn(lxz + lam_y[k]), sr = inv_n * __frcp_rn(lxz + lam_y[r]);
+    const T sk = inv_n * rcp_of(lxz + lam_y[k]), sr = inv_n * rcp_of(lxz + lam_y[r]);
     const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
     // V'_k = conj(w_k)(P_k - i P_r), V'_r = conj(w_r)(P_r - i P_k);  -i z = (z.y, -z.x)
     *Vk = cmul(wkc, cpx<T>{pk.x + pr.y, pk.y - pr.x});
@@ -1162,7 +1175,7 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
   return with_len<T>(g.nz, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
     cudaError_t e;
-    if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
+    if constexpr (has_ct_lengths<T>::value && rgfft::is_rg<N>::value) {
       const int L = rg_lines<N>(tkx);
       const int gr = g.ny * ((nxh + L - 1) / L);
       const size_t smr = rg_smem<T>(N, L);
@@ -1204,11 +1217,13 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
   const size_t sm = zfft_smem<T>(g.ny, tky);
   return with_len<T>(g.ny, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
+    // (FP32 only: the register-staged y pass in pairs needs ~190 registers, one
+    // CTA per SM, and ran 1.6x slower than the shared-memory form at 256^3)
     if constexpr (sizeof(T) == 4 && rgfft::is_rg<N>::value) {
       const int L = rg_lines<N>(tky);
       const int gr = g.nz * ((nxh + L - 1) / L);
       const size_t smr = rg_smem<T>(N, L);
-      if constexpr (N == 256) {
+      if constexpr (N == 256 && sizeof(T) == 4) {
         cudaError_t e = allow_smem(k_ydct256, smr);
         if (e != cudaSuccess) return e;
         k_ydct256<<<gr, L * (N / 16), smr, st>>>(g, (cpx<float>*)spec, (const cpx<float>*)tw,
