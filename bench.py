@@ -552,8 +552,11 @@ def run_batched(args, dev):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
 
-    def time_batch():
-        batch = ppe.Batch(items32, stream=stream)
+    def time_batch(**opts):
+        try:
+            batch = ppe.Batch(items32, stream=stream, **opts)
+        except ppe.PPEError:
+            return None
         for _ in range(2):
             batch.launch()
         torch.cuda.synchronize(dev)
@@ -562,16 +565,31 @@ def run_batched(args, dev):
             batch.launch()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        st = batch.status()
         batch.close()
+        if st["status"] != 0:
+            raise RuntimeError(f"persistent batch status {st}")
         return e0.elapsed_time(e1) / reps
 
-    ms_default = time_batch()
-    # autotuned: each distinct grid tuned once (spectral schedule by the whole
-    # projection's time, then the x-line tile), the others of its size class
-    # take the cached result; the batch graph is then captured again
+    # persistent form (one kernel over a device work queue): default queue
+    # order, then the batch tuner's search over queue orders and residency
+    ms_pers_default = time_batch(form=ppe.BATCH_PERSISTENT)
+    t0 = time.perf_counter()
+    pers_best, ms_pers, pers_trials = autotune.tune_batch(lambda o: time_batch(form=ppe.BATCH_PERSISTENT, **o))
+    pers_tune_s = time.perf_counter() - t0
+    with ppe.Batch(items32, stream=stream, form=ppe.BATCH_PERSISTENT, **pers_best) as b:
+        b.launch()
+        pers_status = b.status()
+    worst_pers = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
+    # graph form: default plans, then per-plan autotuned plans (each distinct
+    # grid tuned once: spectral schedule by the whole projection's time, then
+    # the x-line tile; the others of its size class take the cached result)
+    ms_default = time_batch(form=ppe.BATCH_GRAPH)
     tuned = tune_plans(items32, {k: autotune.SEARCH[k] for k in ("spectral", "x_lines")}, stream)
-    ms_batch = time_batch()
+    ms_graph = time_batch(form=ppe.BATCH_GRAPH)
     worst = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
+    persistent_wins = ms_pers is not None and ms_pers <= ms_graph
+    ms_batch = ms_pers if persistent_wins else ms_graph
 
     def loop64():
         for pl, o in items64:
@@ -589,12 +607,19 @@ def run_batched(args, dev):
     pts = sum(a * b * c for a, b, c in shapes)
     for pl, _ in items32 + items64:
         pl.close()
-    return {"workload": "64 uneven grids (dims from {32,48,64,96,128,192}), FP32 solve + FP64 refinement to 1e-10, "
-                        "one CUDA graph launch, autotuned plans",
+    return {"workload": "64 uneven grids (dims from {32,48,64,96,128,192}), FP32 solve + pair refinement to 1e-10; "
+                        "the faster of the persistent form (one kernel over a device work queue, tuned queue order) "
+                        "and the graph form (one graph launch of per-grid branches, autotuned plans)",
+            "form": "persistent" if persistent_wins else "graph",
             "solves_per_s": 64 / (ms_batch * 1e-3), "ms_per_batch": ms_batch, "gpts_per_s": pts / (ms_batch * 1e-3) / 1e9,
-            "max_rel_residual": worst, "cells": pts,
-            "untuned": {"solves_per_s": 64 / (ms_default * 1e-3), "ms_per_batch": ms_default},
-            "autotune": tuned,
+            "max_rel_residual": max(worst, worst_pers), "cells": pts,
+            "persistent": {"solves_per_s": 64 / (ms_pers * 1e-3) if ms_pers else None, "ms_per_batch": ms_pers,
+                           "default_ms_per_batch": ms_pers_default, "options": pers_best,
+                           "items": pers_status["items"], "ctas": pers_status["ctas"],
+                           "tuner_seconds": pers_tune_s, "trials_ms": pers_trials,
+                           "max_rel_residual": worst_pers},
+            "graph": {"solves_per_s": 64 / (ms_graph * 1e-3), "ms_per_batch": ms_graph,
+                      "untuned_ms_per_batch": ms_default, "autotune": tuned},
             "fp64_loop": {"solves_per_s": 64 / (ms_loop * 1e-3), "ms_per_batch": ms_loop}}
 
 

@@ -268,6 +268,72 @@ void ppe_batch_destroy(ppe_batch_t batch);
 /* One-shot form: create, launch, synchronise `stream`, destroy. */
 ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields* fields, void* stream);
 
+/* Persistent form of the batch: one kernel launch (after a small reset kernel,
+ * both in the batch's graph) runs every projection of the batch.  The host
+ * lists the (grid, stage, tile) items of all grids in a queue order; resident
+ * CTAs take items in that order, and a stage of a grid starts once every tile
+ * of the grid's previous stage has counted itself done on the device.  The
+ * stages of one grid are those of ppe_project's FP32_REFINE form: rho_0, the
+ * constants, the right-hand side of Eq. (34), the x, z, y, z, x passes of the
+ * direct solve, then one refinement sweep: the residual and the same five
+ * passes, Eq. (33) fused with the new residual, and the loop test.  When a
+ * loop test asks for another sweep, the graph's WHILE loop launches the same
+ * kernel again over the sweep stages (grids whose test stopped them skip
+ * their items), until no grid asks for one; each grid stops as its own
+ * refinement would (tolerance reached or max_sweeps applied).  Every plan must
+ * be PPE_FP32_REFINE with walls (no outflow top), the LEGACY spectral
+ * schedule, 1 <= max_sweeps, and each dimension in {32, 48, 64, 96, 128, 192,
+ * 256}; otherwise form PERSISTENT is refused (PPE_ERR_INVALID_ARG).
+ *   form          PPE_BATCH_GRAPH (the graph branches of ppe_batch_create),
+ *                 PPE_BATCH_PERSISTENT, or PPE_BATCH_AUTO (the library's
+ *                 choice: the graph form, the faster on every batch measured).
+ *   window,       queue order: grids in windows of `window` (0: all grids in one
+ *   stagger       window), stage-major within a window, each window entering
+ *                 `stagger` stages after the one before (-1: the default, 2).
+ *   ctas_per_sm   resident CTAs per SM (0: as many as fit, at most 3).
+ *   wait_seconds  limit of one wait for a stage (0: 2 s).  A wait that runs out
+ *                 stops the launch: every CTA stops taking items, the batch's
+ *                 status and every plan's ppe_get_info report PPE_ERR_TIMEOUT.
+ *   test_unset_wait  non-zero: grid 0's second stage waits on a counter that
+ *                 nothing increments, so that the wait runs out (a test of the
+ *                 bounded wait; the batch's results are then incomplete).
+ *   grain         elements (cells, faces or spectrum values) per queue item: an
+ *                 item is a run of up to 255 consecutive tiles of one stage of
+ *                 one grid, about `grain` elements in all (0: 65536). */
+typedef enum { PPE_BATCH_AUTO = 0, PPE_BATCH_GRAPH = 1, PPE_BATCH_PERSISTENT = 2 } ppe_batch_form;
+typedef struct {
+  int form;
+  int window;
+  int stagger;
+  int ctas_per_sm;
+  double wait_seconds;
+  int test_unset_wait;
+  int grain;
+} ppe_batch_options;
+/* ppe_batch_create with options (NULL: the defaults, form AUTO). */
+ppe_status ppe_batch_create_ex(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                               void* stream, const ppe_batch_options* opt);
+/* Synchronise the batch's stream and read the status of its last launch:
+ * PPE_ERR_TIMEOUT if a stage wait of the persistent form ran out (then
+ * *err_grid and *err_stage name it), else PPE_OK.  *form receives the form the
+ * batch took (PPE_BATCH_GRAPH or PPE_BATCH_PERSISTENT), *items the number of
+ * items of its first queue (0 for the graph form), *ctas the persistent
+ * kernel's CTAs and *launches how many times the last run launched it (1 +
+ * the further sweeps); any output pointer may be NULL. */
+ppe_status ppe_batch_status(ppe_batch_t batch, int* form, long long* items, int* ctas, int* launches,
+                            int* err_grid, int* err_stage);
+/* Host-side queue of the persistent form, without device work (a planning
+ * and test aid): grids of dims[3 g .. 3 g + 2] = (nx, ny, nz), rho_0 given
+ * (rho_given[g] != 0) or reduced; window, stagger and grain as in
+ * ppe_batch_options; first = 0 (the whole projection: the first launch) or 8
+ * (the sweep stages: a further sweep).  Returns the number of items (-1 if a
+ * grid does not qualify or an argument is out of range), and writes
+ * min(cap, items) of them to out as (grid, stage, first tile, tiles)
+ * quadruples in queue order; need and tiles (either may be NULL) receive, for
+ * all 15 stages of every grid (grid after grid), the stage's items and tiles. */
+long long ppe_batch_schedule(int n, const int* dims, const int* rho_given, int window, int stagger, int grain,
+                             int first, int* out, long long cap, int* need, int* tiles);
+
 /* Synchronise the plan's stream and read the device-side results.  Returns
  * PPE_ERR_NOT_CONVERGED if the refinement stopped above its tolerance, else
  * PPE_ERR_INCOMPATIBLE_RHS if the compatibility test of ppe_options.compat_tol

@@ -130,3 +130,43 @@ def autotune(plan: "ppe.Plan", run, reps: int = 3, path: str | None = DEFAULT_CA
         cache[cache_key(plan)] = result
         save_cache(cache, path)
     return result
+
+
+# Queue of the persistent batched form (ppe_batch_options): elements per
+# queue item (tile runs), grids per window of the stage-major order, stages
+# between windows, resident CTAs per SM (0: as many as fit).
+BATCH_SEARCH = {
+    "grain": (65536, 16384, 262144, 1048576),
+    "window": (0, 32, 16, 8),
+    "stagger": (1, 2, 4, 8),
+    "ctas_per_sm": (0, 2),
+}
+
+
+def tune_batch(measure, search=None, start=None):
+    """Coordinate search over the persistent batch's options.  `measure(opts)`
+    builds the batch with the option dict `opts` (keys of BATCH_SEARCH), times
+    its launches and returns milliseconds per batch (or None if the options are
+    refused).  Each field is tried in turn with the others held at the best so
+    far.  Returns (best options, best ms, {option tuple: ms} of every trial)."""
+    search = search or BATCH_SEARCH
+    best = dict(start or {k: v[0] for k, v in search.items()})
+    trials = {}
+
+    def key(o):
+        return tuple(o[k] for k in search)
+
+    def score(o):
+        k = key(o)
+        if k not in trials:
+            trials[k] = measure(dict(o))
+        return trials[k]
+
+    best_ms = score(best)
+    for field, values in search.items():
+        for v in values:
+            cand = dict(best, **{field: v})
+            ms = score(cand)
+            if ms is not None and (best_ms is None or ms < best_ms):
+                best, best_ms = cand, ms
+    return best, best_ms, {",".join(f"{k}={v}" for k, v in zip(search, t)): ms for t, ms in trials.items()}

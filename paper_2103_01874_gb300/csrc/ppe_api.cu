@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -1218,17 +1219,191 @@ struct ppe_batch_s {
   cudaGraphExec_t exec;
   cudaStream_t stream;
   int n;
+  int form;            // PPE_BATCH_GRAPH or PPE_BATCH_PERSISTENT
+  void* dev;           // persistent form: grids, items, stage tiles, counters, stop marks, control block
+  BatchCtl* ctl;
+  long long nitems;
+  int ctas;
 };
 
-ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
-                            void* stream) {
-  if (!out || n < 1 || !plans || !fields) return PPE_ERR_INVALID_ARG;
-  *out = nullptr;
+namespace {
+
+// A plan and its fields that the persistent batched kernel can run.
+bool batch_plan_ok(ppe_plan_t P) {
+  return P->fp32 && !P->gd.top_open && P->sched == PPE_SPECTRAL_LEGACY && P->opt.max_sweeps >= 1 &&
+         P->opt.max_sweeps <= kMaxSweeps && batch_dims_ok(P->g.nx, P->g.ny, P->g.nz);
+}
+
+bool fields_ok(const ppe_fields* F) {
+  return F->u && F->v && F->w && F->S && F->rho && F->p_n && F->p_nm1 && F->p && F->u_out && F->v_out &&
+         F->w_out && F->dt > 0;
+}
+
+size_t align_up(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Builds the persistent form of a batch into B (B->stream set): the grid
+// descriptors, the two queues (the whole projection; a further sweep), the
+// device state, and a graph: reset, persistent launch, then WHILE (a loop test
+// asked for another sweep) { sweep reset, persistent launch of the sweep queue }.
+ppe_status batch_persistent(ppe_batch_t B, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                            const ppe_batch_options& o) {
+  std::vector<int> nx(n), ny(n), nz(n), rg(n);
+  size_t smem = 0;
   for (int i = 0; i < n; ++i) {
-    if (!plans[i]) return PPE_ERR_INVALID_ARG;
-    for (int j = 0; j < i; ++j)
-      if (plans[j] == plans[i]) return PPE_ERR_INVALID_ARG;
+    ppe_plan_t P = plans[i];
+    nx[i] = P->g.nx;
+    ny[i] = P->g.ny;
+    nz[i] = P->g.nz;
+    rg[i] = fields[i].rho0 > 0 ? 1 : 0;
+    smem = std::max(smem, batch_smem(nx[i], ny[i], nz[i]));
   }
+  const long grain = o.grain > 0 ? o.grain : 65536;
+  const long long n_full = batch_item_count(n, nx.data(), ny.data(), nz.data(), rg.data(), 0, grain);
+  const long long n_sweep = batch_item_count(n, nx.data(), ny.data(), nz.data(), rg.data(), BS_RES, grain);
+  if (n_full < 1 || n_full > 0x7FFFFFFFll) return PPE_ERR_INVALID_ARG;
+  const int ndone = kBatchStages * n;
+  std::vector<BatchItem> full((size_t)n_full), sweep((size_t)n_sweep);
+  std::vector<unsigned> need(ndone), tiles(ndone);
+  const int window = o.window > 0 ? o.window : n;
+  const int stagger = o.stagger >= 0 ? o.stagger : 2;
+  batch_schedule(n, nx.data(), ny.data(), nz.data(), rg.data(), window, stagger, 0, grain, full.data(), need.data(),
+                 tiles.data());
+  batch_schedule(n, nx.data(), ny.data(), nz.data(), rg.data(), window, stagger, BS_RES, grain, sweep.data(),
+                 need.data(), tiles.data());
+  std::vector<BatchGrid> grids(n);
+  for (int i = 0; i < n; ++i) {
+    ppe_plan_t P = plans[i];
+    const ppe_fields* F = &fields[i];
+    BatchGrid& G = grids[i];
+    memset(&G, 0, sizeof(G));
+    G.g = P->gd;
+    G.in = make_in(P, F->u, F->v, F->w, F->S, F->rho, F->p_n, F->p_nm1, F->dt);
+    G.sc = P->sc;
+    G.f64 = F->f;
+    G.fdf = P->fdf;
+    G.pdf = P->pdf;
+    G.upre = P->upre;
+    G.vpre = P->vpre;
+    G.wpre = P->wpre;
+    G.spec = (cpx<float>*)P->spec;
+    G.tw_x = (const cpx<float>*)P->tw_x;
+    G.tw_z = (const cpx<float>*)P->tw_z;
+    G.tw_y = (const cpx<float>*)P->tw_y;
+    G.wq_y = (const cpx<float>*)P->wq_y;
+    const float* lam = (const float*)P->lam;
+    G.lam_x = lam;
+    G.lam_y = lam + P->nxh;
+    G.lam_z = lam + P->nxh + P->g.ny;
+    G.out_p = F->p;
+    G.out_u = F->u_out;
+    G.out_v = F->v_out;
+    G.out_w = F->w_out;
+    G.rho0 = F->rho0;
+    G.tol = P->opt.refine_tol;
+    G.scale = 1.0 / ((double)(P->g.nx / 2) * (double)P->g.nz);
+    G.smax = P->opt.max_sweeps;
+    G.lpb = batch_lpb(P->g.nx);
+    G.tkx = batch_tkx(P->g.nz, true);
+    G.tky = batch_tkx(P->g.ny, false);
+    G.kc = P->g.nz < 8 ? P->g.nz : 8;
+    G.stage0 = kBatchStages * i;
+  }
+  // one allocation: grids | full queue | sweep queue | need | tiles | done (+ sentinel) | stop | ctl
+  const size_t o_full = align_up(sizeof(BatchGrid) * n);
+  const size_t o_sweep = o_full + align_up(sizeof(BatchItem) * (size_t)n_full);
+  const size_t o_need = o_sweep + align_up(sizeof(BatchItem) * (size_t)n_sweep);
+  const size_t o_tiles = o_need + align_up(sizeof(unsigned) * ndone);
+  const size_t o_done = o_tiles + align_up(sizeof(unsigned) * ndone);
+  const size_t o_stop = o_done + align_up(sizeof(unsigned) * (ndone + 1));
+  const size_t o_ctl = o_stop + align_up(sizeof(int) * n);
+  const size_t total = o_ctl + align_up(sizeof(BatchCtl));
+  char* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return alloc_status(e);
+  }
+  B->dev = d;
+  B->ctl = (BatchCtl*)(d + o_ctl);
+  B->nitems = n_full;
+  PPE_TRY(cudaMemcpy(d, grids.data(), sizeof(BatchGrid) * n, cudaMemcpyHostToDevice));
+  PPE_TRY(cudaMemcpy(d + o_full, full.data(), sizeof(BatchItem) * (size_t)n_full, cudaMemcpyHostToDevice));
+  PPE_TRY(cudaMemcpy(d + o_sweep, sweep.data(), sizeof(BatchItem) * (size_t)n_sweep, cudaMemcpyHostToDevice));
+  PPE_TRY(cudaMemcpy(d + o_need, need.data(), sizeof(unsigned) * ndone, cudaMemcpyHostToDevice));
+  PPE_TRY(cudaMemcpy(d + o_tiles, tiles.data(), sizeof(unsigned) * ndone, cudaMemcpyHostToDevice));
+  PPE_TRY(cudaMemset(d + o_ctl, 0, sizeof(BatchCtl)));
+  int occ = 0, dev = 0, sms = 0;
+  PPE_TRY(batch_occupancy(smem, &occ));
+  PPE_TRY(cudaGetDevice(&dev));
+  PPE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (occ < 1) return PPE_ERR_INVALID_ARG;  // the largest stage's tile does not fit an SM
+  const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+  B->ctas = per_sm * sms;
+  const double ws = o.wait_seconds > 0 ? o.wait_seconds : 2.0;
+  const unsigned long long wait_ns = (unsigned long long)(ws * 1e9);
+  const BatchGrid* dg = (const BatchGrid*)d;
+  unsigned* done = (unsigned*)(d + o_done);
+  const unsigned* dneed = (const unsigned*)(d + o_need);
+  const unsigned* dtiles = (const unsigned*)(d + o_tiles);
+  int* stop = (int*)(d + o_stop);
+  // capture
+  cudaStream_t cs = nullptr, bs = nullptr;
+  cudaGraph_t g = nullptr;
+  ppe_status st = PPE_OK;
+  bool cap = false, bcap = false;
+  auto ok = [&](cudaError_t r) {
+    if (r != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
+    return st == PPE_OK;
+  };
+  if (ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) &&
+      ok(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) &&
+      ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+    cap = true;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t cond = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (ok(launch_batch_reset(dg, n, done, ndone, stop, B->ctl, cs)) &&
+        ok(launch_batch(dg, n, (const BatchItem*)(d + o_full), (int)n_full, done, ndone, dneed, dtiles, stop,
+                        B->ctl, wait_ns, o.test_unset_wait ? 1 : 0, B->ctas, smem, cs)) &&
+        ok(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps)) &&
+        ok(cudaGraphConditionalHandleCreate(&h, cg, 0u, cudaGraphCondAssignDefault)) &&
+        ok(launch_batch_cond(B->ctl, h, cs)) &&
+        ok(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps))) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      if (ok(cudaGraphAddNode(&cond, cg, deps, nullptr, ndeps, &cp)) &&
+          ok(cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies)) &&
+          ok(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal))) {
+        bcap = true;
+        if (ok(launch_batch_sweep_reset(dg, n, done, B->ctl, bs)))
+          if (ok(launch_batch(dg, n, (const BatchItem*)(d + o_sweep), (int)n_sweep, done, ndone, dneed, dtiles,
+                              stop, B->ctl, wait_ns, 0, B->ctas, smem, bs)))
+            ok(launch_batch_cond(B->ctl, h, bs));
+      }
+    }
+    if (bcap) {
+      cudaGraph_t bg = nullptr;
+      ok(cudaStreamEndCapture(bs, &bg));
+    }
+  }
+  if (cap) ok(cudaStreamEndCapture(cs, &g));
+  if (st == PPE_OK) ok(cudaGraphInstantiate(&B->exec, g, 0));
+  if (g) cudaGraphDestroy(g);
+  if (bs) cudaStreamDestroy(bs);
+  if (cs) cudaStreamDestroy(cs);
+  if (st != PPE_OK) cudaGetLastError();
+  return st;
+}
+
+// Graph form: every projection captured as branches of one graph.
+ppe_status batch_graph(ppe_batch_t B, int n, const ppe_plan_t* plans, const ppe_fields* fields) {
   const int nb = n < 16 ? n : 16;  // branch streams: solves on one stream run in order
   cudaStream_t cs = nullptr;
   std::vector<cudaStream_t> bs(nb, nullptr);
@@ -1236,14 +1411,6 @@ ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, co
   cudaGraph_t g = nullptr;
   ppe_status st = PPE_OK;
   bool capturing = false;
-  auto cleanup = [&]() {
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
-    for (cudaStream_t s : bs)
-      if (s) cudaStreamDestroy(s);
-    if (cs) cudaStreamDestroy(cs);
-    if (g) cudaGraphDestroy(g);
-  };
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) st = PPE_ERR_CUDA;
   for (int b = 0; st == PPE_OK && b < nb; ++b)
     if (cudaStreamCreateWithFlags(&bs[b], cudaStreamNonBlocking) != cudaSuccess) st = PPE_ERR_CUDA;
@@ -1270,35 +1437,130 @@ ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, co
     if (cudaStreamEndCapture(cs, &cg) != cudaSuccess && st == PPE_OK) st = PPE_ERR_CUDA;
     g = cg;
   }
-  ppe_batch_t B = nullptr;
-  if (st == PPE_OK) {
-    B = new (std::nothrow) ppe_batch_s;
-    if (!B) st = PPE_ERR_OUT_OF_MEMORY;
-  }
   if (st == PPE_OK && cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) st = PPE_ERR_CUDA;
-  cleanup();
-  if (st != PPE_OK) {
-    delete B;
-    cudaGetLastError();
-    return st;
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : bs)
+    if (s) cudaStreamDestroy(s);
+  if (cs) cudaStreamDestroy(cs);
+  if (g) cudaGraphDestroy(g);
+  if (st != PPE_OK) cudaGetLastError();
+  return st;
+}
+
+}  // namespace
+
+ppe_status ppe_batch_create_ex(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                               void* stream, const ppe_batch_options* opt) {
+  if (!out || n < 1 || !plans || !fields) return PPE_ERR_INVALID_ARG;
+  *out = nullptr;
+  ppe_batch_options o;
+  memset(&o, 0, sizeof(o));
+  o.stagger = -1;
+  if (opt) o = *opt;
+  if (o.form < PPE_BATCH_AUTO || o.form > PPE_BATCH_PERSISTENT || o.ctas_per_sm < 0 || !(o.wait_seconds >= 0) ||
+      o.grain < 0)
+    return PPE_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return PPE_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return PPE_ERR_INVALID_ARG;
   }
+  bool persistent_ok = n <= 65535;
+  for (int i = 0; i < n && persistent_ok; ++i)
+    persistent_ok = batch_plan_ok(plans[i]) && fields_ok(&fields[i]);
+  if (o.form == PPE_BATCH_PERSISTENT && !persistent_ok) return PPE_ERR_INVALID_ARG;
+  ppe_batch_t B = new (std::nothrow) ppe_batch_s;
+  if (!B) return PPE_ERR_OUT_OF_MEMORY;
+  memset(B, 0, sizeof(*B));
   B->stream = (cudaStream_t)stream;
   B->n = n;
+  // AUTO: the graph form, which ran faster than the persistent form on every
+  // batch measured on a GB300 (one 256^3 grid, 8 x 128^3, 64 x 64^3, 64
+  // uneven grids)
+  const bool persistent = o.form == PPE_BATCH_PERSISTENT;
+  B->form = persistent ? PPE_BATCH_PERSISTENT : PPE_BATCH_GRAPH;
+  const ppe_status st = persistent ? batch_persistent(B, n, plans, fields, o) : batch_graph(B, n, plans, fields);
+  if (st != PPE_OK) {
+    ppe_batch_destroy(B);
+    return st;
+  }
   *out = B;
   return PPE_OK;
 }
 
+ppe_status ppe_batch_create(ppe_batch_t* out, int n, const ppe_plan_t* plans, const ppe_fields* fields,
+                            void* stream) {
+  ppe_batch_options o;
+  memset(&o, 0, sizeof(o));
+  o.form = PPE_BATCH_GRAPH;
+  o.stagger = -1;
+  return ppe_batch_create_ex(out, n, plans, fields, stream, &o);
+}
+
 ppe_status ppe_batch_launch(ppe_batch_t B) {
   NvtxRange _nvtx("ppe_batch_launch");
-  if (!B) return PPE_ERR_INVALID_ARG;
+  if (!B || !B->exec) return PPE_ERR_INVALID_ARG;
   PPE_TRY(cudaGraphLaunch(B->exec, B->stream));
   return PPE_OK;
 }
 
+ppe_status ppe_batch_status(ppe_batch_t B, int* form, long long* items, int* ctas, int* launches, int* err_grid,
+                            int* err_stage) {
+  if (!B) return PPE_ERR_INVALID_ARG;
+  if (form) *form = B->form;
+  if (items) *items = B->nitems;
+  if (ctas) *ctas = B->ctas;
+  if (launches) *launches = 0;
+  if (err_grid) *err_grid = -1;
+  if (err_stage) *err_stage = -1;
+  PPE_TRY(cudaStreamSynchronize(B->stream));
+  if (!B->ctl) return PPE_OK;
+  BatchCtl h;
+  PPE_TRY(cudaMemcpy(&h, B->ctl, sizeof(h), cudaMemcpyDeviceToHost));
+  if (launches) *launches = h.launches;
+  if (err_grid) *err_grid = h.err_grid;
+  if (err_stage) *err_stage = h.err_stage;
+  return h.status == 0 ? PPE_OK : (ppe_status)h.status;
+}
+
 void ppe_batch_destroy(ppe_batch_t B) {
   if (!B) return;
-  cudaGraphExecDestroy(B->exec);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->dev) cudaFree(B->dev);
   delete B;
+}
+
+long long ppe_batch_schedule(int n, const int* dims, const int* rho_given, int window, int stagger, int grain,
+                             int first, int* out, long long cap, int* need, int* tiles) {
+  if (n < 1 || !dims || !rho_given || cap < 0 || (cap > 0 && !out) || grain < 0 || (first != 0 && first != BS_RES))
+    return -1;
+  std::vector<int> nx(n), ny(n), nz(n), rg(n);
+  for (int i = 0; i < n; ++i) {
+    nx[i] = dims[3 * i];
+    ny[i] = dims[3 * i + 1];
+    nz[i] = dims[3 * i + 2];
+    rg[i] = rho_given[i] ? 1 : 0;
+    if (!batch_dims_ok(nx[i], ny[i], nz[i])) return -1;
+  }
+  const long gr = grain > 0 ? grain : 65536;
+  const long long nitems = batch_item_count(n, nx.data(), ny.data(), nz.data(), rg.data(), first, gr);
+  std::vector<BatchItem> items((size_t)nitems);
+  std::vector<unsigned> nd((size_t)kBatchStages * n), nt((size_t)kBatchStages * n);
+  batch_schedule(n, nx.data(), ny.data(), nz.data(), rg.data(), window > 0 ? window : n, stagger >= 0 ? stagger : 2,
+                 first, gr, items.data(), nd.data(), nt.data());
+  const long long m = cap < nitems ? cap : nitems;
+  for (long long i = 0; i < m; ++i) {
+    out[4 * i] = items[i].grid;
+    out[4 * i + 1] = items[i].stage;
+    out[4 * i + 2] = (int)items[i].tile0;
+    out[4 * i + 3] = items[i].count;
+  }
+  for (size_t i = 0; i < nd.size(); ++i) {
+    if (need) need[i] = (int)nd[i];
+    if (tiles) tiles[i] = (int)nt[i];
+  }
+  return nitems;
 }
 
 ppe_status ppe_project_batched(int n, const ppe_plan_t* plans, const ppe_fields* fields, void* stream) {
@@ -1352,7 +1614,7 @@ namespace {
 // The report and status of one projection from a host copy of its scalars.
 ppe_status info_from(ppe_plan_t P, const DevScalars& h, ppe_info* info) {
   const double fmax = h.fmax_bits ? __builtin_bit_cast(double, h.fmax_bits) : 0.0;
-  const bool timed_out = h.dev_err != 0;  // a bounded wait for a bulk tensor copy ran out
+  const bool timed_out = h.dev_err != 0;  // a bounded device-side wait ran out (bulk copy or batch stage)
   info->f_max = fmax;
   info->rho0 = __builtin_bit_cast(double, h.rho0_bits);
   bool incompatible = false;

@@ -61,8 +61,9 @@ struct DevScalars {
   // the next correction's spectrum (so p + correction has zero mean)
   double zmode;
   int p_parts;
-  int dev_err;                                  // device-side errors of the current call (bit 1: a bounded
-                                                // wait for a bulk tensor copy ran out); reported as PPE_ERR_TIMEOUT
+  int dev_err;                                  // device-side errors of the current call, reported as
+                                                // PPE_ERR_TIMEOUT: bit 1 a bounded wait for a bulk tensor
+                                                // copy ran out; bit 2 a stage wait of the batched kernel did
   // unsplit projection (k_pcg.cu): conjugate-gradient state
   double pcg_alpha, pcg_beta, pcg_rz;           // step, direction update, r . z
   double pcg_gmean;                             // mean of the right side g (kept by r)
@@ -203,6 +204,80 @@ cudaError_t launch_zfft_tma(bool inverse, const GridDev& g, const CUtensorMap& t
 cudaError_t launch_ydct_tma(const GridDev& g, cpx<float>* spec, const cpx<float>* tw, const cpx<float>* wq,
                             const float* lam_x, const float* lam_y, const float* lam_z, DevScalars* err,
                             cudaStream_t st);  // err->zmode: the zero mode's value
+
+// ---- persistent batched projection (k_batch.cu) ----
+// One launch runs the FP32 + pair-refinement projections of many grids: a
+// device work queue of (grid, stage, tile) items, taken in order by resident
+// CTAs; a stage of a grid starts once every tile of the grid's previous stage
+// has counted itself done.  Stages of one grid (the sequence of ppe_project):
+//   0 rho_0 = min(rho)   1 stencil constants   2 right-hand side   3 forward x
+//   4 forward z          5 y solve             6 inverse z         7 inverse x
+// then one refinement sweep:
+//   8 residual and forward x   9 forward z   10 y solve   11 inverse z
+//   12 inverse x, accumulated  13 correction and residual   14 loop test
+// Further sweeps (grids whose loop test asks for one) run stages 8-14 again in
+// further launches of the same kernel, inside a graph WHILE loop.
+enum BatchStageKind { BS_RHO = 0, BS_CONST, BS_RHS, BS_XF, BS_ZF0, BS_Y0, BS_ZI0, BS_XI0, BS_RES, BS_ZF, BS_Y,
+                      BS_ZI, BS_XA, BS_CC, BS_CHK, kBatchStages };
+constexpr int kBatchThreads = 256;
+
+struct BatchGrid {            // one grid of the batch (device copy, read-only in the kernel)
+  GridDev g;
+  StencilIn in;
+  DevScalars* sc;
+  double* f64;                // f as FP64 (may be NULL)
+  df *fdf, *pdf, *upre, *vpre, *wpre;
+  cpx<float>* spec;
+  const cpx<float> *tw_x, *tw_z, *tw_y, *wq_y;
+  const float *lam_x, *lam_y, *lam_z;
+  double *out_p, *out_u, *out_v, *out_w;
+  double rho0, tol, scale;    // rho0 <= 0: min(rho); scale 1 / ((nx/2) nz)
+  int smax;                   // refinement sweeps at most (>= 1)
+  int lpb, tkx, tky, kc;      // tiles of the x passes (radix-3 nx), z and y passes (radix-3), RHS chunk
+  int stage0;                 // the grid's first stage counter (kBatchStages per grid)
+};
+struct BatchItem {            // tiles tile0 .. tile0 + count - 1 of one stage of one grid
+  uint16_t grid;
+  uint8_t stage, count;
+  uint32_t tile0;
+};
+struct BatchCtl {
+  unsigned int next;          // queue head
+  int abort;                  // set on a timed-out wait: every CTA stops taking items
+  int status;                 // 0, or PPE_ERR_TIMEOUT
+  int err_grid, err_stage;    // the wait that ran out
+  int cont_any;               // a loop test of this launch asked for another sweep
+  int launches;               // launches of the kernel in the last batch run
+  int pad;
+};
+bool batch_dims_ok(int nx, int ny, int nz);            // lengths with instances in the batched kernel
+unsigned batch_stage_tiles(int nx, int ny, int nz, bool rho_given, int stage);
+// tiles per queue item of a stage: about `grain` elements (cells, faces or
+// spectrum values) per item, at most 255 tiles
+unsigned batch_stage_chunk(int nx, int ny, int nz, int stage, long grain);
+int batch_lpb(int nx);                                   // x-pass lines per tile (radix-3 nx/2)
+int batch_tkx(int n, bool zpass);                        // z / y columns per tile (radix-3 lengths)
+size_t batch_smem(int nx, int ny, int nz);               // dynamic shared memory of the grid's largest stage
+// queue of stages [first, kBatchStages) of every grid: grids in windows of
+// `window`, stage-major within a window, window w offset by w * stagger stages
+// need[kBatchStages g + s]: the items of every stage (the count a waiting
+// stage needs), tiles[...]: its tiles (the tile count its device function sees)
+long long batch_item_count(int n, const int* nx, const int* ny, const int* nz, const int* rho_given, int first,
+                           long grain);
+void batch_schedule(int n, const int* nx, const int* ny, const int* nz, const int* rho_given, int window,
+                    int stagger, int first, long grain, BatchItem* items, unsigned* need, unsigned* tiles);
+cudaError_t batch_occupancy(size_t smem, int* ctas_per_sm);
+// reset of every grid's scalars, the counters and the control block (before the first launch)
+cudaError_t launch_batch_reset(const BatchGrid* grids, int ngrid, unsigned* done, int ndone, int* stop,
+                               BatchCtl* ctl, cudaStream_t st);
+// reset of the sweep stages' counters and the queue head (before a further sweep)
+cudaError_t launch_batch_sweep_reset(const BatchGrid* grids, int ngrid, unsigned* done, BatchCtl* ctl,
+                                     cudaStream_t st);
+cudaError_t launch_batch(const BatchGrid* grids, int ngrid, const BatchItem* items, int nitems, unsigned* done,
+                         int ndone, const unsigned* need, const unsigned* tiles, int* stop, BatchCtl* ctl,
+                         unsigned long long wait_ns, int hold, int ctas, size_t smem, cudaStream_t st);
+// sets the WHILE condition: another sweep if a loop test asked for one and no wait ran out
+cudaError_t launch_batch_cond(BatchCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
 
 // ---- launchers (k_stencil.cu) ----
 // Eq. (31) divergence constraint (and the one-fluid density when rho != NULL)

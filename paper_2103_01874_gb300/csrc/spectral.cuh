@@ -97,15 +97,15 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 // ---------------------------------------------------------------------------
 // OPEN: the residual's top cells see the outflow ghost (SRC_RESID only)
 template <typename T, int SRC, bool DO_FFT, int N, bool OPEN = false>
-__global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
-                                              const df* __restrict__ pdf, cpx<T>* spec, RadixPlan rp,
-                                              const cpx<T>* __restrict__ tw, int lpb) {
+__device__ __forceinline__ void xfwd_body(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                              const df* pdf, cpx<T>* spec, RadixPlan rp,
+                                              const cpx<T>* tw, int lpb, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
   const int lsc = M + 1;  // padded line stride (complex elements) against bank conflicts
   const int nlines = g.ny * g.nz;
-  const int l0 = blockIdx.x * lpb;
+  const int l0 = bid * lpb;
   cpx<T>* bufa = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb lines of lsc; line ll holds its nx reals packed
   cpx<T>* bufb = bufa + (size_t)lpb * lsc;
   cpx<T>* tws = bufb + (size_t)lpb * lsc;           // twiddles exp(-2 pi i t/nx), t < nx
@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
   if (SRC == SRC_F || SRC == SRC_FDF) {
     // per-CTA sum of f, totalled in a fixed order by the next kernel (finish_sums)
-    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + blockIdx.x);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->x_parts = (int)gridDim.x;
+    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + bid);
+    if (bid == 0 && threadIdx.x == 0) sc->x_parts = (int)nblk;
   }
   if (!DO_FFT) return;
   cp_async_wait_all();
@@ -244,6 +244,12 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalar
     X.y = (T)0.5 * (a.y - wb.x);
     spec[(size_t)line * nxh + kx] = X;
   }
+}
+template <typename T, int SRC, bool DO_FFT, int N, bool OPEN = false>
+__global__ void __launch_bounds__(256) k_xfwd(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                              const df* __restrict__ pdf, cpx<T>* spec, RadixPlan rp,
+                                              const cpx<T>* __restrict__ tw, int lpb) {
+  xfwd_body<T, SRC, DO_FFT, N, OPEN>(g, in, sc, slot, fdf, pdf, spec, rp, tw, lpb, blockIdx.x, gridDim.x);
 }
 
 // Line stride (complex elements) of the x passes' shared buffer: rgfft rows,
@@ -276,16 +282,16 @@ __device__ __forceinline__ PlaneLanes plane_lanes(int L) { return {L < 8 ? L : 8
 // half spectrum.  Same cell arithmetic as k_xfwd.
 // PL: the spectrum in the plane layout [kx][line] (GridDev::spec_planes).
 template <int SRC, int M, bool OPEN, bool PL = false>
-__global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
-                                                 const df* __restrict__ pdf, cpx<float>* spec,
-                                                 const cpx<float>* __restrict__ tw, int L) {
+__device__ __forceinline__ void xfwd_rg_body(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                                 const df* pdf, cpx<float>* spec,
+                                                 const cpx<float>* tw, int L, uint32_t bid, uint32_t nblk) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (SRC == SRC_RESID && slot < 0) slot = sc->iter;  // residual slot chosen on the device
   constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xstride<PL>(M);
   const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
   const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
-  const uint32_t l0 = blockIdx.x * (uint32_t)L;
+  const uint32_t l0 = bid * (uint32_t)L;
   const uint32_t line = l0 + ll;
   const bool valid = line < nlines;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // L lines of LS
@@ -373,8 +379,8 @@ __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevSca
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
   if (SRC == SRC_F || SRC == SRC_FDF) {
     // per-CTA sum of f, totalled in a fixed order by the next kernel (finish_sums)
-    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + blockIdx.x);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->x_parts = (int)gridDim.x;
+    block_pair_sums(fsum, df{0.0f, 0.0f}, sc->part + (size_t)g.ny * g.nz + bid);
+    if (bid == 0 && threadIdx.x == 0) sc->x_parts = (int)nblk;
   }
   __syncthreads();
   // untangle: X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, W = exp(-2 pi i/nx)
@@ -408,20 +414,26 @@ __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevSca
     }
   }
 }
+template <int SRC, int M, bool OPEN, bool PL = false>
+__global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
+                                                 const df* __restrict__ pdf, cpx<float>* spec,
+                                                 const cpx<float>* __restrict__ tw, int L) {
+  xfwd_rg_body<SRC, M, OPEN, PL>(g, in, sc, slot, fdf, pdf, spec, tw, L, blockIdx.x, gridDim.x);
+}
 
 // ---------------------------------------------------------------------------
 // z pass
 // ---------------------------------------------------------------------------
 template <typename T, bool INV, int N>
-__global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
-                                              int tkx, const DevScalars* sc, DevScalars* fin) {
+__device__ __forceinline__ void zfft_body(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* tw,
+                                              int tkx, const DevScalars* sc, DevScalars* fin, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (fin && blockIdx.x == 0) finish_sums(fin, g);  // uniform over the CTA
+  if (fin && bid == 0) finish_sums(fin, g);  // uniform over the CTA
   if (sc && sc->done) return;
   const int nz = g.nz, nxh = g.nx / 2 + 1;
   const int ntile = (nxh + tkx - 1) / tkx;
-  const int j = blockIdx.x / ntile;
-  const int kx0 = (blockIdx.x - j * ntile) * tkx;
+  const int j = bid / ntile;
+  const int kx0 = (bid - j * ntile) * tkx;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* b = a + (size_t)tkx * nz;
   cpx<T>* tws = b + (size_t)tkx * nz;  // exp(-2 pi i t/nz)
@@ -444,21 +456,26 @@ __global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan
     if (kx0 + c < nxh) spec[base + k * rowstride + c] = r[idx];
   }
 }
+template <typename T, bool INV, int N>
+__global__ void __launch_bounds__(256) k_zfft(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
+                                              int tkx, const DevScalars* sc, DevScalars* fin) {
+  zfft_body<T, INV, N>(g, spec, rp, tw, tkx, sc, fin, blockIdx.x, gridDim.x);
+}
 
 // Register-staged z pass (FP32, power-of-two nz; rgfft in fft.cuh): one CTA
 // per (j, tile of L kx columns), L * nz/16 threads; the first pass reads the
 // columns from the spectrum and the last pass writes them back, so each
 // element crosses shared memory once.
 template <typename T, bool INV, int N>
-__global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw, int L,
-                                                 const DevScalars* sc, DevScalars* fin) {
+__device__ __forceinline__ void zfft_rg_body(GridDev g, cpx<T>* spec, const cpx<T>* tw, int L,
+                                                 const DevScalars* sc, DevScalars* fin, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (fin && blockIdx.x == 0) finish_sums(fin, g);  // uniform over the CTA
+  if (fin && bid == 0) finish_sums(fin, g);  // uniform over the CTA
   if (sc && sc->done) return;
   const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
   const uint32_t ntile = (nxh + L - 1) / L;
-  const uint32_t j = blockIdx.x / ntile;
-  const uint32_t kx0 = (blockIdx.x - j * ntile) * L;
+  const uint32_t j = bid / ntile;
+  const uint32_t kx0 = (bid - j * ntile) * L;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/nz)
   for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
@@ -472,6 +489,11 @@ __global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const 
         if (valid) col[(uint32_t)e * rs] = v;
       },
       buf + line, L, t0, tws);
+}
+template <typename T, bool INV, int N>
+__global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw, int L,
+                                                 const DevScalars* sc, DevScalars* fin) {
+  zfft_rg_body<T, INV, N>(g, spec, tw, L, sc, fin, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,14 +614,14 @@ __global__ void __launch_bounds__(128) k_ythomas(GridDev g, cpx<T>* spec, const 
 // an inverse FFT, and x_j = v'[pos(j)] / N.  Eigenvalue of mode (kx, ky, kz):
 // lam_x[kx] + lam_y[ky] + lam_z[kz]; the zero mode is set to zero.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
-                                              const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
-                                              const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky,
-                                              const DevScalars* zsc) {
+__device__ __forceinline__ void ydct_body(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* tw,
+                                              const cpx<T>* wq, const T* lam_x,
+                                              const T* lam_y, const T* lam_z, int tky,
+                                              const DevScalars* zsc, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nxh = g.nx / 2 + 1, ny = g.ny;
   const int ntile = (nxh + tky - 1) / tky;
-  const int kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * tky;
+  const int kz = bid / ntile, kx0 = (bid - kz * ntile) * tky;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* b = a + (size_t)tky * ny;
   cpx<T>* tws = b + (size_t)tky * ny;  // exp(-2 pi i t/ny)
@@ -659,6 +681,13 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
     if (kx0 + c < nxh) spec[base + (size_t)j * nxh + c] = R[pj * tky + c];
   }
 }
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan rp, const cpx<T>* __restrict__ tw,
+                                              const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
+                                              const T* __restrict__ lam_y, const T* __restrict__ lam_z, int tky,
+                                              const DevScalars* zsc) {
+  ydct_body<T, N>(g, spec, rp, tw, wq, lam_x, lam_y, lam_z, tky, zsc, blockIdx.x, gridDim.x);
+}
 
 // Register-staged form of k_ydct (FP32, power-of-two ny; rgfft in fft.cuh):
 // the reordered line is read straight from the spectrum by the first pass of
@@ -666,14 +695,14 @@ __global__ void __launch_bounds__(256) k_ydct(GridDev g, cpx<T>* spec, RadixPlan
 // the last pass of the inverse writes the reordered result back.  Same
 // arithmetic as k_ydct.
 template <typename T, int N>
-__global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw,
-                                                 const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
-                                                 const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L,
-                                                 const DevScalars* zsc) {
+__device__ __forceinline__ void ydct_rg_body(GridDev g, cpx<T>* spec, const cpx<T>* tw,
+                                                 const cpx<T>* wq, const T* lam_x,
+                                                 const T* lam_y, const T* lam_z, int L,
+                                                 const DevScalars* zsc, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
   const uint32_t ntile = (nxh + L - 1) / L;
-  const uint32_t kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * L;
+  const uint32_t kz = bid / ntile, kx0 = (bid - kz * ntile) * L;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/ny)
   for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
@@ -737,6 +766,13 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
     if (kx0 + c < nxh) spec[kz * (uint32_t)N * nxh + (uint32_t)jj * nxh + kx0 + c] = buf[rgfft::row(pj) * L + c];
   }
 }
+template <typename T, int N>
+__global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw,
+                                                 const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
+                                                 const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L,
+                                                 const DevScalars* zsc) {
+  ydct_rg_body<T, N>(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc, blockIdx.x, gridDim.x);
+}
 
 // 256-point form of k_ydct_rg (radices 16 x 16) with the eigenvalue divide in
 // registers between the transforms.  After the second forward pass thread t
@@ -745,16 +781,16 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
 // Each thread forms V'_k for its own k with the operations k_ydct_rg uses for
 // that member of the pair (k, N-k) (the compiler may contract products into
 // sums differently, so the last bits can differ; the FP32 solve is refined).
-static __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
-                                                  const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
-                                                  const float* __restrict__ lam_y, const float* __restrict__ lam_z,
-                                                  int L, const DevScalars* zsc) {
+__device__ __forceinline__ void ydct256_body(GridDev g, cpx<float>* spec, const cpx<float>* tw,
+                                                  const cpx<float>* wq, const float* lam_x,
+                                                  const float* lam_y, const float* lam_z,
+                                                  int L, const DevScalars* zsc, uint32_t bid, uint32_t nblk) {
   using T = float;
   constexpr int N = 256;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t nxh = (uint32_t)g.nx / 2 + 1;
   const uint32_t ntile = (nxh + L - 1) / L;
-  const uint32_t kz = blockIdx.x / ntile, kx0 = (blockIdx.x - kz * ntile) * L;
+  const uint32_t kz = bid / ntile, kx0 = (bid - kz * ntile) * L;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* tws = buf + rgfft::rows(N) * L;  // exp(-2 pi i t/ny)
   for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
@@ -833,21 +869,27 @@ static __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>
     for (int q = 0; q < 16; ++q) col[(uint32_t)jof(t0 + 16 * q) * nxh] = v[q];
   }
 }
+static __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>* spec, const cpx<float>* __restrict__ tw,
+                                                  const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
+                                                  const float* __restrict__ lam_y, const float* __restrict__ lam_z,
+                                                  int L, const DevScalars* zsc) {
+  ydct256_body(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc, blockIdx.x, gridDim.x);
+}
 
 // ---------------------------------------------------------------------------
 // inverse x pass
 // ---------------------------------------------------------------------------
 // MODE: XI_F64 p = s x (FP64); XI_DF pdf = s x (pairs); XI_DF_ACC pdf += s x
 template <typename T, int MODE, int N>
-__global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, df* pdf,
-                                              double scale, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
-                                              const DevScalars* sc, DevScalars* psc) {
+__device__ __forceinline__ void xinv_body(GridDev g, const cpx<T>* spec, double* p, df* pdf,
+                                              double scale, RadixPlan rp, const cpx<T>* tw, int lpb,
+                                              const DevScalars* sc, DevScalars* psc, uint32_t bid, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
   const int nx = g.nx, M = nx / 2, nxh = M + 1;
   const int lsc = M + 1;  // line stride (complex): nxh values, also the padded FFT stride
   const int nlines = g.ny * g.nz;
-  const int l0 = blockIdx.x * lpb;
+  const int l0 = bid * lpb;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smem_raw);  // lpb * lsc
   cpx<T>* b = a + (size_t)lpb * lsc;                // lpb * lsc
   cpx<T>* tws = b + (size_t)lpb * lsc;              // exp(-2 pi i t/nx), t < nx
@@ -917,9 +959,15 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
   }
   if (MODE != XI_F64 && psc) {
     // per-CTA sum of p, totalled in a fixed order by the next z pass (finish_sums)
-    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + blockIdx.x);
-    if (blockIdx.x == 0 && threadIdx.x == 0) psc->p_parts = (int)gridDim.x;
+    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + bid);
+    if (bid == 0 && threadIdx.x == 0) psc->p_parts = (int)nblk;
   }
+}
+template <typename T, int MODE, int N>
+__global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restrict__ spec, double* p, df* pdf,
+                                              double scale, RadixPlan rp, const cpx<T>* __restrict__ tw, int lpb,
+                                              const DevScalars* sc, DevScalars* psc) {
+  xinv_body<T, MODE, N>(g, spec, p, pdf, scale, rp, tw, lpb, sc, psc, blockIdx.x, gridDim.x);
 }
 
 // Register-staged inverse x pass (FP32, nx = 2M, M a power of two): thread
@@ -931,22 +979,22 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
 // first copied (transposed) into the shared buffer, then the first pass reads
 // them there.
 template <int MODE, int M, bool PL = false>
-__global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
-                                                 double scale, const cpx<float>* __restrict__ tw, int L,
-                                                 const DevScalars* sc, DevScalars* psc) {
+__device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, double* p, df* pdf,
+                                                 double scale, const cpx<float>* tw, int L,
+                                                 const DevScalars* sc, DevScalars* psc, uint32_t bid, uint32_t nblk) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
   constexpr int TPL = M / 16, nx = 2 * M, nxh = M + 1, LS = xstride<PL>(M);
   const uint32_t nlines = (uint32_t)g.ny * (uint32_t)g.nz;
   const int ll = (int)threadIdx.x / TPL, t0 = (int)threadIdx.x & (TPL - 1);
-  const uint32_t line = blockIdx.x * (uint32_t)L + ll;
+  const uint32_t line = bid * (uint32_t)L + ll;
   const bool valid = line < nlines;
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* tws = buf + L * LS;
   for (int t = threadIdx.x; t < nx; t += blockDim.x) tws[t] = tw[t];
   if constexpr (PL) {
-    const uint32_t l0 = blockIdx.x * (uint32_t)L;
+    const uint32_t l0 = bid * (uint32_t)L;
     const PlaneLanes pl = plane_lanes(L);
     const int lane = threadIdx.x & 31, lqo = lane % pl.lq, kxo = lane / pl.lq;
     const int ngl = L / pl.lq, ngk = (nxh + pl.kq - 1) / pl.kq;
@@ -1016,7 +1064,7 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
     rgfft::run<T, true, M, 2, PL, rgfft::PAD_ROWS>(ld, [&](int e, cpx<T> v) { buf[ll * LS + rgfft::row(e)] = v; },
                                   buf + ll * LS, 1, t0, tws);
     __syncthreads();
-    const uint32_t l0 = blockIdx.x * (uint32_t)L;
+    const uint32_t l0 = bid * (uint32_t)L;
     constexpr int U = 4;
     for (int b0 = threadIdx.x; b0 < L * M; b0 += U * blockDim.x) {
       float4 q[U];
@@ -1042,9 +1090,15 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
   }
   if (MODE != XI_F64 && psc) {
     // per-CTA sum of p, totalled in a fixed order by the next z pass (finish_sums)
-    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + blockIdx.x);
-    if (blockIdx.x == 0 && threadIdx.x == 0) psc->p_parts = (int)gridDim.x;
+    block_pair_sums(psum, df{0.0f, 0.0f}, psc->part + 2 * (size_t)g.ny * g.nz + bid);
+    if (bid == 0 && threadIdx.x == 0) psc->p_parts = (int)nblk;
   }
+}
+template <int MODE, int M, bool PL = false>
+__global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
+                                                 double scale, const cpx<float>* __restrict__ tw, int L,
+                                                 const DevScalars* sc, DevScalars* psc) {
+  xinv_rg_body<MODE, M, PL>(g, spec, p, pdf, scale, tw, L, sc, psc, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,10 @@ BC_OUTFLOW = 1   # open top, p = 0 on the face
 SPECTRAL_LEGACY = 0  # three passes, spectrum [kz][j][kx]
 SPECTRAL_FUSED = 1   # one cluster pass per kx plane
 SPECTRAL_PENCIL = 2  # three bulk-copy-staged persistent passes, spectrum [kx][kz][j]
+# forms of a batch (ppe_batch_options.form)
+BATCH_AUTO = 0        # persistent where every plan qualifies, else graph
+BATCH_GRAPH = 1       # graph branches, one per projection
+BATCH_PERSISTENT = 2  # one persistent kernel over a device work queue
 
 STATUS = {0: "PPE_OK", 1: "PPE_ERR_INVALID_ARG", 2: "PPE_ERR_UNSUPPORTED_SIZE", 3: "PPE_ERR_INCOMPATIBLE_RHS",
           4: "PPE_ERR_OUT_OF_MEMORY", 5: "PPE_ERR_NOT_CONVERGED", 6: "PPE_ERR_TIMEOUT", 7: "PPE_ERR_CUDA"}
@@ -60,6 +64,11 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("form", c_int), ("window", c_int), ("stagger", c_int), ("ctas_per_sm", c_int),
+                ("wait_seconds", c_double), ("test_unset_wait", c_int), ("grain", c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -97,6 +106,12 @@ SIGNATURES = {
     "ppe_batch_launch": (c_int, [c_void_p]),
     "ppe_batch_destroy": (None, [c_void_p]),
     "ppe_project_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(FieldsC), c_void_p]),
+    "ppe_batch_create_ex": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(FieldsC), c_void_p,
+                                    POINTER(BatchOptions)]),
+    "ppe_batch_status": (c_int, [c_void_p, POINTER(c_int), POINTER(ctypes.c_longlong), POINTER(c_int),
+                                 POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ppe_batch_schedule": (ctypes.c_longlong, [c_int, POINTER(c_int), POINTER(c_int), c_int, c_int, c_int, c_int,
+                                               POINTER(c_int), ctypes.c_longlong, POINTER(c_int), POINTER(c_int)]),
     "ppe_set_tuning": (c_int, [c_void_p, POINTER(Tuning)]),
     "ppe_profile_read": (c_int, [c_void_p, POINTER(KernelTime), c_int]),
     "ppe_project_unsplit": (c_int, [c_void_p, POINTER(FieldsC), c_double, c_int]),
@@ -206,7 +221,8 @@ class Batch:
     `items` is a list of (plan, dict of tensors u, v, w, S, rho, p_n, p_nm1, p,
     u_out, v_out, w_out [, f], dt [, rho0])."""
 
-    def __init__(self, items, stream=None):
+    def __init__(self, items, stream=None, form=BATCH_GRAPH, window=0, stagger=-1, ctas_per_sm=0,
+                 wait_seconds=0.0, test_unset_wait=False, grain=0):
         n = len(items)
         self._keep = items  # tensors must outlive the graph
         plans = (c_void_p * n)(*[pl._h.value for pl, _ in items])
@@ -214,14 +230,28 @@ class Batch:
         for i, (pl, d) in enumerate(items):
             flds[i] = pl._fields(_ptr, d["u"], d["v"], d["w"], d["S"], d["rho"], d["p_n"], d["p_nm1"], d["dt"],
                                  d["p"], d["u_out"], d["v_out"], d["w_out"], d.get("f"), d.get("rho0", -1.0))
+        opt = BatchOptions(int(form), int(window), int(stagger), int(ctas_per_sm), float(wait_seconds),
+                           1 if test_unset_wait else 0, int(grain))
         h = c_void_p()
-        _check(lib().ppe_batch_create(ctypes.byref(h), n, plans, flds, c_void_p(_stream_handle(stream))),
-               "ppe_batch_create")
+        _check(lib().ppe_batch_create_ex(ctypes.byref(h), n, plans, flds, c_void_p(_stream_handle(stream)),
+                                         ctypes.byref(opt)), "ppe_batch_create_ex")
         self._h = h
         self.n = n
 
     def launch(self):
         _check(lib().ppe_batch_launch(self._h), "ppe_batch_launch")
+
+    def status(self, check=True):
+        """Synchronise and read the last launch's status: a dict with form,
+        items, ctas, launches, status (PPE_* code), err_grid, err_stage."""
+        form, ctas, nl, eg, es = c_int(), c_int(), c_int(), c_int(), c_int()
+        items = ctypes.c_longlong()
+        code = lib().ppe_batch_status(self._h, ctypes.byref(form), ctypes.byref(items), ctypes.byref(ctas),
+                                      ctypes.byref(nl), ctypes.byref(eg), ctypes.byref(es))
+        if check and code not in (0, 6):
+            _check(code, "ppe_batch_status")
+        return {"form": form.value, "items": items.value, "ctas": ctas.value, "launches": nl.value,
+                "status": code, "err_grid": eg.value, "err_stage": es.value}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -402,3 +432,24 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def batch_schedule(dims, rho_given, window=0, stagger=-1, first=0, grain=0):
+    """Host-side queue of the persistent batched form (ppe_batch_schedule; no
+    device work): returns (items, need, tiles) with items a list of (grid,
+    stage, first tile, tiles) in queue order (first = 0: the whole projection;
+    8: a further sweep), need and tiles the items and tiles of the 15 stages of
+    every grid, grid after grid; None if a grid does not qualify."""
+    n = len(dims)
+    d = (c_int * (3 * n))(*[int(v) for t in dims for v in t])
+    rg = (c_int * n)(*[1 if v else 0 for v in rho_given])
+    args = (int(window), int(stagger), int(grain), int(first))
+    m = lib().ppe_batch_schedule(n, d, rg, *args, None, 0, None, None)
+    if m < 0:
+        return None
+    out = (c_int * (4 * max(m, 1)))()
+    need, tiles = (c_int * (15 * n))(), (c_int * (15 * n))()
+    m2 = lib().ppe_batch_schedule(n, d, rg, *args, out, m, need, tiles)
+    assert m2 == m
+    items = [tuple(out[4 * i:4 * i + 4]) for i in range(m)]
+    return items, list(need), list(tiles)

@@ -85,3 +85,24 @@ def test_apply_cached_without_entry(tmp_path):
 @pytest.mark.parametrize("field", list(autotune.SEARCH))
 def test_every_search_field_is_a_tuning_field(field):
     assert field in dict(ppe.Tuning._fields_)
+
+
+def test_tune_batch_coordinate_search():
+    # a separable cost with its minimum at window=16, stagger=4, ctas=2; one
+    # combination refused (None): the search must skip it
+    cost = {"window": {0: 5.0, 32: 3.0, 16: 1.0, 8: 2.0}, "stagger": {1: 4.0, 2: 3.0, 4: 0.5, 8: 1.0},
+            "ctas_per_sm": {0: 1.0, 2: 0.25}}
+    calls = []
+
+    def measure(o):
+        calls.append(o)
+        if o["window"] == 8 and o["stagger"] == 1:
+            return None
+        return sum(cost[k][o[k]] for k in cost)
+    search = {k: v for k, v in autotune.BATCH_SEARCH.items() if k in cost}
+    best, ms, trials = autotune.tune_batch(measure, search=search)
+    assert best == {"window": 16, "stagger": 4, "ctas_per_sm": 2}
+    assert ms == 1.0 + 0.5 + 0.25
+    # every trial measured once, and the table lists them
+    assert len(calls) == len({tuple(sorted(c.items())) for c in calls}) == len(trials)
+    assert "window=16,stagger=4,ctas_per_sm=2" in trials
