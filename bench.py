@@ -40,14 +40,16 @@ N_CELLS = NX * NY * NZ
 F_BYTES = 8 * N_CELLS
 
 
-def set_grid(n: int):
-    """Grid edge for profiling runs of a smaller case (the bench line itself is 256^3)."""
+def set_grid(nx: int, ny: int | None = None, nz: int | None = None):
+    """Grid of profiling runs of a smaller case (the bench line itself is 256^3)."""
     global NX, NY, NZ, N_CELLS, F_BYTES, WORKLOAD
-    NX = NY = NZ = n
-    N_CELLS = n ** 3
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    NX, NY, NZ = nx, ny, nz
+    N_CELLS = nx * ny * nz
     F_BYTES = 8 * N_CELLS
-    if n != 256:
-        WORKLOAD = (f"multimode {n}x{n}x{n} (profiling case), density 640/60, FP32 solve + FP64 refinement "
+    if (nx, ny, nz) != (256, 256, 256):
+        WORKLOAD = (f"multimode {nx}x{ny}x{nz} (profiling case), density 640/60, FP32 solve + FP64 refinement "
                     f"to rel residual 1e-10")
 
 
@@ -221,7 +223,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    if NX == 256:
+    if (NX, NY, NZ) == (256, 256, 256):
         fl = fields.multimode_256(seed=replica_seed(rank))
     else:
         fl = fields.make_fields(NX, NY, NZ, seed=replica_seed(rank), recipe="multimode", width=6.0, rho_g=60.0)
@@ -823,6 +825,8 @@ def main():
     ap.add_argument("--cpu-solves", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=256, help="grid edge (profiling runs only; the bench line is 256)")
+    ap.add_argument("--shape", default=None,
+                    help="NX,NY,NZ of a profiling run (overrides --n; the bench line is 256,256,256)")
     ap.add_argument("--forms", default="fp32,fp64", help="fp32 (always) and/or fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-times", dest="kernel_times", action="store_false")
@@ -836,7 +840,10 @@ def main():
                     help="drive every timed step with per-kernel events (refinement loop from the host), so that a "
                          "profiler sees each kernel as its own launch")
     args = ap.parse_args()
-    set_grid(args.n)
+    if args.shape:
+        set_grid(*[int(v) for v in args.shape.split(",")])
+    else:
+        set_grid(args.n)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
