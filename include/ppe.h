@@ -365,18 +365,27 @@ void ppe_destroy(ppe_plan_t plan);
  *               nz in {32, 64, 128, 256} and nx/2 a power of two in [16, 512].
  *               LEGACY is the default of every plan; ppe_get_tuning reports
  *               the schedule in use.
+ *   y_solve     method of the LEGACY schedule's y step in a PPE_FP32_REFINE plan
+ *               with walls (PPE_Y_*): COSINE, the DCT-II, eigenvalue divide and
+ *               DCT-III through FFTs; TRIDIAGONAL, the Thomas elimination of the
+ *               Neumann system with tabulated multipliers, written as two affine
+ *               scans over 16-element segments of each line (ny <= 512), the
+ *               singular line kx = kz = 0 solved in FP64.  COSINE is the
+ *               default; other plans report and accept COSINE only.
  * The first five are tile sizes and change no result bit.  The schedules run
  * the same arithmetic, but the compiler may contract the FP32 products of the
- * y pass differently, so their FP32 solves can differ in the last bits; the
- * refined results then agree to the refinement's tolerance.
+ * y pass differently, and the two y methods round differently, so their FP32
+ * solves can differ in the last bits; the refined results then agree to the
+ * refinement's tolerance.
  * ppe_set_tuning returns PPE_ERR_INVALID_ARG (and changes nothing) if a value
  * is outside its range, a schedule is not available for the plan, or a pass
  * would need more than 227 KB of shared memory per CTA.  Synchronises the
  * plan's stream (captured refinement graphs are rebuilt with the new
  * schedule). */
 enum { PPE_SPECTRAL_LEGACY = 0, PPE_SPECTRAL_FUSED = 1, PPE_SPECTRAL_PENCIL = 2 };
+enum { PPE_Y_COSINE = 0, PPE_Y_TRIDIAGONAL = 1 };
 typedef struct {
-    int rhs_lines, rhs_planes, x_lines, z_cols, y_cols, spectral;
+    int rhs_lines, rhs_planes, x_lines, z_cols, y_cols, spectral, y_solve;
 } ppe_tuning;
 ppe_status ppe_get_tuning(ppe_plan_t plan, ppe_tuning* out);
 ppe_status ppe_set_tuning(ppe_plan_t plan, const ppe_tuning* tuning);

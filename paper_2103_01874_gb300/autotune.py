@@ -32,6 +32,7 @@ STEP = "step"  # score: the sum of all kernel times of the projection
 # order: the schedule decides which kernels the later fields drive)
 SEARCH = {
     "spectral": (STEP, (0, 1, 2)),
+    "y_solve": (STEP, (1, 0)),
     "rhs_lines": ("k_rhs_march", (1, 2, 4, 8)),
     "rhs_planes": ("k_rhs_march", (4, 8, 16, 32)),
     "x_lines": ("k_xinv", (4, 8, 16, 32, 64)),

@@ -55,6 +55,10 @@ struct ppe_plan_s {
   bool zyz_ok;
   bool pencil_ok;
   int sched;
+  // y step of the LEGACY schedule (ppe_tuning.y_solve): PPE_Y_TRIDIAGONAL where
+  // yscan_ok (FP32_REFINE, walls, ny <= 512: Thomas tables built)
+  bool yscan_ok;
+  int y_solve;
   alignas(64) CUtensorMap tmap;
   alignas(64) CUtensorMap tmap_z;
   // refinement loops as CUDA graphs with a WHILE conditional node (FP32_REFINE):
@@ -439,7 +443,10 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
   }
   PPE_LAUNCH(P, K_ZFFT_FWD,
              launch_zfft<T>(false, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, fin, P->stream));
-  if ((P->fp32 || P->pairs) && !P->gd.top_open) {  // DCT-II/III for walls; the open top: tridiagonal solve
+  if (P->y_solve == PPE_Y_TRIDIAGONAL) {  // (FP32, walls) the Thomas elimination in scan form
+    PPE_LAUNCH(P, K_YTHOMAS, launch_ythomas_scan(P->gd, (cpx<float>*)spec, (const float*)P->tab, P->line_off,
+                                                 P->line_len, (float)P->a_y, P->sc, P->stream));
+  } else if ((P->fp32 || P->pairs) && !P->gd.top_open) {  // DCT-II/III for walls; the open top: tridiagonal solve
     const T* lam = (const T*)P->lam;
     PPE_LAUNCH(P, K_YTHOMAS, launch_ydct<T>(P->gd, spec, P->rp_y, (const cpx<T>*)P->tw_y, (const cpx<T>*)P->wq_y,
                                             lam, lam + P->nxh, lam + P->nxh + P->g.ny, P->tky, P->sc, P->stream));
@@ -875,6 +882,11 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       s = make_twiddles<float>(&P->tw_x, g->nx);
       if (s == PPE_OK) s = make_twiddles<float>(&P->tw_z, g->nz);
       if (s == PPE_OK) s = P->gd.top_open ? make_thomas<float>(P) : make_dct_tables<float>(P);
+      // walls: the multipliers of the tridiagonal y method too (PPE_Y_TRIDIAGONAL)
+      if (s == PPE_OK && !P->gd.top_open && yscan_elems(g->ny) > 0) {
+        s = make_thomas<float>(P);
+        P->yscan_ok = s == PPE_OK;
+      }
       if (s == PPE_OK) s = cuda_status(set_smem_limits<float>());
     } else if (P->pairs) {
       s = make_twiddles<dd>(&P->tw_x, g->nx);
@@ -904,6 +916,9 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
       P->pencil_ok = make_spec_tmap(P, &P->tmap_z, pencil_zcols(g->ny, g->nz));
   }
   set_sched(P, PPE_SPECTRAL_LEGACY);
+  // COSINE by default: at 256^3 on a GB300 its y pass takes 58 us against 84 us
+  // for the tridiagonal scans (ppe_set_tuning / the autotuner choose per grid)
+  P->y_solve = PPE_Y_COSINE;
   if (s == PPE_OK && P->fp32) s = build_refine_graphs(P);
   if (s == PPE_OK) s = cuda_status(launch_init_scalars(P->sc, 1.0, o.refine_tol, 0, P->stream));
   if (s == PPE_OK)
@@ -980,6 +995,7 @@ ppe_status ppe_get_tuning(ppe_plan_t P, ppe_tuning* t) {
   t->z_cols = P->tkx;
   t->y_cols = P->tky;
   t->spectral = P->sched;
+  t->y_solve = P->y_solve;
   return PPE_OK;
 }
 
@@ -995,6 +1011,7 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
   if (!pow2(t->x_lines, 1, 64)) return PPE_ERR_INVALID_ARG;
   if (!pow2(t->z_cols, 1, 16) || !pow2(t->y_cols, 1, 32)) return PPE_ERR_INVALID_ARG;
   if (!sched_ok(P, t->spectral)) return PPE_ERR_INVALID_ARG;
+  if (t->y_solve != PPE_Y_COSINE && !(t->y_solve == PPE_Y_TRIDIAGONAL && P->yscan_ok)) return PPE_ERR_INVALID_ARG;
   const size_t xs = P->fp32 ? (xfwd_smem<float>(nx, t->x_lines) > xinv_smem<float>(nx, t->x_lines)
                                    ? xfwd_smem<float>(nx, t->x_lines) : xinv_smem<float>(nx, t->x_lines))
                             : (xfwd_smem<double>(nx, t->x_lines) > xinv_smem<double>(nx, t->x_lines)
@@ -1018,6 +1035,7 @@ ppe_status ppe_set_tuning(ppe_plan_t P, const ppe_tuning* t) {
     P->tkx = u.z_cols;
     P->tky = u.y_cols;
     set_sched(P, u.spectral);
+    P->y_solve = u.y_solve;
     return P->fp32 ? build_refine_graphs(P) : PPE_OK;
   };
   const ppe_status s = apply(*t);

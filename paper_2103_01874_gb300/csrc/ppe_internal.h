@@ -184,6 +184,12 @@ size_t xpass_smem_limit();  // largest dynamic shared memory of the x passes (st
 template <typename T>
 size_t zpass_smem_limit();  // the same for the z pass
 
+// ---- tridiagonal y solve in scan form, FP32 with walls (k_yscan.cu) ----
+int yscan_elems(int ny);  // elements per thread (0: ny above 512, not supported)
+// zsc->zmode: the mean given to the singular line kx = kz = 0 (keeps p zero-mean)
+cudaError_t launch_ythomas_scan(const GridDev& g, cpx<float>* spec, const float* tab, const int* line_off,
+                                const int* line_len, float a, const DevScalars* zsc, cudaStream_t st);
+
 // ---- fused z-y-z pass on the plane layout (k_zyz.cu) ----
 bool zyz_supported(int ny, int nz);  // ny, nz in {32, 64, 128, 256}
 int zyz_cols(int ny, int nz);        // j columns per CTA (the bulk tensor box width)

@@ -28,6 +28,9 @@ BC_OUTFLOW = 1   # open top, p = 0 on the face
 SPECTRAL_LEGACY = 0  # three passes, spectrum [kz][j][kx]
 SPECTRAL_FUSED = 1   # one cluster pass per kx plane
 SPECTRAL_PENCIL = 2  # three bulk-copy-staged persistent passes, spectrum [kx][kz][j]
+# y step of the LEGACY schedule (ppe_tuning.y_solve)
+Y_COSINE = 0       # DCT-II, eigenvalue divide, DCT-III through FFTs
+Y_TRIDIAGONAL = 1  # Thomas elimination as two affine scans (FP32 with walls, ny <= 512)
 # forms of a batch (ppe_batch_options.form)
 BATCH_AUTO = 0        # persistent where every plan qualifies, else graph
 BATCH_GRAPH = 1       # graph branches, one per projection
@@ -60,7 +63,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("rhs_lines", c_int), ("rhs_planes", c_int), ("x_lines", c_int), ("z_cols", c_int),
-                ("y_cols", c_int), ("spectral", c_int)]
+                ("y_cols", c_int), ("spectral", c_int), ("y_solve", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

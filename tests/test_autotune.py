@@ -16,9 +16,10 @@ class FakePlan:
         face_rule = 0
 
     def __init__(self):
-        self.t = dict(rhs_lines=2, rhs_planes=8, x_lines=16, z_cols=16, y_cols=8, spectral=0)
+        self.t = dict(rhs_lines=2, rhs_planes=8, x_lines=16, z_cols=16, y_cols=8, spectral=0, y_solve=1)
         self.on = False
         self.rec = {}
+        self.tri_us = 35  # the tridiagonal y method's time
 
     def get_tuning(self):
         return dict(self.t)
@@ -44,7 +45,8 @@ class FakePlan:
         c = {"k_rhs_march": 300 + 20 * abs(t["rhs_lines"] - 4) + abs(t["rhs_planes"] - 16),
              "k_xinv": 40 + abs(t["x_lines"] - 8)}
         if t["spectral"] == 0:
-            c.update(k_zfft_fwd=30 + abs(t["z_cols"] - 4), k_ysolve=60 + abs(t["y_cols"] - 16), k_zfft_inv=27)
+            ys = 60 + abs(t["y_cols"] - 16) if t["y_solve"] == 0 else self.tri_us
+            c.update(k_zfft_fwd=30 + abs(t["z_cols"] - 4), k_ysolve=ys, k_zfft_inv=27)
         else:
             c.update(k_zfft_fwd=25, k_ysolve=55, k_zfft_inv=20)  # PENCIL: faster here
         return c
@@ -106,3 +108,21 @@ def test_tune_batch_coordinate_search():
     # every trial measured once, and the table lists them
     assert len(calls) == len({tuple(sorted(c.items())) for c in calls}) == len(trials)
     assert "window=16,stagger=4,ctas_per_sm=2" in trials
+
+
+class LegacyOnly(FakePlan):
+    def set_tuning(self, **kw):
+        if kw.get("spectral", self.t["spectral"]) != 0:
+            raise ppe.PPEError(1, "ppe_set_tuning")
+        super().set_tuning(**kw)
+
+
+@pytest.mark.parametrize("tri_us,expect", [(35, 1), (90, 0)])
+def test_y_method_by_whole_step_time(tmp_path, tri_us, expect):
+    plan = LegacyOnly()
+    plan.tri_us = tri_us
+    res = autotune.autotune(plan, plan.run, reps=2, path=str(tmp_path / "t.json"))
+    assert res["tuning"]["spectral"] == 0
+    assert res["tuning"]["y_solve"] == expect
+    if expect == 0:  # with the cosine method the y column count matters again
+        assert res["tuning"]["y_cols"] == 16

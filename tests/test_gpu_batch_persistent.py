@@ -31,6 +31,9 @@ def _setup(shapes=SHAPES, max_sweeps=4, rules=None, rho_given=None):
         rule = (rules[n] if rules else (ppe.FACE_HARMONIC if n % 3 == 2 else ppe.FACE_ARITHMETIC))
         plan = ppe.Plan(nx, ny, nz, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, face_rule=rule,
                         max_sweeps=max_sweeps)
+        # the persistent kernel's y step is the cosine method: the graph form
+        # compared with it takes the same
+        plan.set_tuning(y_solve=ppe.Y_COSINE)
         d = {k: torch.from_numpy(v.copy()).to("cuda") for k, v in fl.arrays().items()}
         d.update(p=torch.empty(fl.shape, dtype=torch.float64, device="cuda"), u_out=torch.empty_like(d["u"]),
                  v_out=torch.empty_like(d["v"]), w_out=torch.empty_like(d["w"]),
@@ -176,6 +179,7 @@ def test_further_sweeps_run_in_the_loop():
         pl.close()
         p2 = ppe.Plan(fl.nx, fl.ny, fl.nz, fl.lx, fl.ly, fl.lz, precision=ppe.FP32_REFINE, face_rule=rule,
                       max_sweeps=3, refine_tol=tol)
+        p2.set_tuning(y_solve=ppe.Y_COSINE)
         rebuilt.append((p2, d, rule))
     items = rebuilt
     pairs = [(pl, d) for pl, d, _ in items]
