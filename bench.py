@@ -587,7 +587,7 @@ def run_batched(args, dev):
     # grid tuned once: spectral schedule by the whole projection's time, then
     # the x-line tile; the others of its size class take the cached result)
     ms_default = time_batch(form=ppe.BATCH_GRAPH)
-    tuned = tune_plans(items32, {k: autotune.SEARCH[k] for k in ("spectral", "x_lines")}, stream)
+    tuned = tune_plans(items32, {k: autotune.SEARCH[k] for k in ("spectral", "y_solve", "x_lines")}, stream)
     ms_graph = time_batch(form=ppe.BATCH_GRAPH)
     worst = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
     persistent_wins = ms_pers is not None and ms_pers <= ms_graph
@@ -643,7 +643,10 @@ def tune_plans(items, search, stream, path=None):
                     plan.project(o["u"], o["v"], o["w"], o["S"], o["rho"], o["p_n"], o["p_nm1"], o["dt"], o["p"],
                                  o["u_out"], o["v_out"], o["w_out"])
             autotune.autotune(plan, run, reps=2, path=path, search=search)
-        name = {0: "legacy", 1: "fused", 2: "pencil"}[plan.get_tuning()["spectral"]]
+        t = plan.get_tuning()
+        name = {0: "legacy", 1: "fused", 2: "pencil"}[t["spectral"]]
+        if t["spectral"] == 0:
+            name += "+" + ("tridiagonal" if t["y_solve"] == 1 else "cosine")
         chosen[name] = chosen.get(name, 0) + 1
     return {"search": list(search), "schedules_chosen": chosen, "seconds": time.perf_counter() - t0,
             "cache": path}

@@ -254,7 +254,8 @@ ppe_status ppe_unsplit_info(ppe_plan_t plan, int* iterations, double* rel_residu
 /* Batched projections (many grids of any sizes in one launch).  Each plan
  * (distinct; a plan may appear once per batch) is paired with its fields.
  * ppe_batch_create captures the projections once into a CUDA graph whose
- * independent branches run concurrently; every ppe_batch_launch then replays
+ * independent branches (up to 16, the projections balanced over them by
+ * cells, largest first) run concurrently; every ppe_batch_launch then replays
  * the whole batch with one graph launch on `stream`.  The field pointers are
  * baked into the graph: launch again only with the same buffers (their
  * contents may change).  Per-plan results (ppe_get_info) are valid after the

@@ -154,8 +154,9 @@ long long batch_item_count(int n, const int* nx, const int* ny, const int* nz, c
 // window has its stage s listed before any of its stage s + 1), window w
 // entering `stagger` stages after window w - 1, so that several windows'
 // stages are in flight at once while each window's spectra stay few enough to
-// be reused from L2.  Ties: grid index, then tile.  A grid's stages keep their
-// order, so every item's dependency is listed before it.  need and tiles are
+// be reused from L2.  Ties: larger grids first, then grid index, then tile.  A
+// grid's stages keep their order, so every item's dependency is listed before
+// it.  need and tiles are
 // filled for every stage (also those before `first`).
 void batch_schedule(int n, const int* nx, const int* ny, const int* nz, const int* rho_given, int window,
                     int stagger, int first, long grain, BatchItem* items, unsigned* need, unsigned* tiles) {
@@ -176,8 +177,13 @@ void batch_schedule(int n, const int* nx, const int* ny, const int* nz, const in
   std::vector<Key> keys;
   for (int g = 0; g < n; ++g)
     for (int s = first; s < kBatchStages; ++s) keys.push_back({(long long)s + (long long)stagger * (g / window), g, s});
-  std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
-    return a.k != b.k ? a.k < b.k : (a.g != b.g ? a.g < b.g : a.s < b.s);
+  // within a key, larger grids first: their longer chains of stages start
+  // earlier (then grid index, stage)
+  auto cells = [&](int g) { return (double)nx[g] * ny[g] * nz[g]; };
+  std::stable_sort(keys.begin(), keys.end(), [&](const Key& a, const Key& b) {
+    if (a.k != b.k) return a.k < b.k;
+    if (cells(a.g) != cells(b.g)) return cells(a.g) > cells(b.g);
+    return a.g != b.g ? a.g < b.g : a.s < b.s;
   });
   size_t m = 0;
   for (const Key& k : keys) {

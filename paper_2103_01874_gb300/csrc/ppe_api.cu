@@ -1439,10 +1439,24 @@ ppe_status batch_graph(ppe_batch_t B, int n, const ppe_plan_t* plans, const ppe_
   if (st == PPE_OK && cudaEventRecord(ev[nb], cs) != cudaSuccess) st = PPE_ERR_CUDA;
   for (int b = 0; st == PPE_OK && b < nb; ++b)
     if (cudaStreamWaitEvent(bs[b], ev[nb], 0) != cudaSuccess) st = PPE_ERR_CUDA;
-  for (int i = 0; st == PPE_OK && i < n; ++i) {
+  // branches balanced by cells: largest grid first, each to the branch with the
+  // least work so far (a branch runs its projections in order, so the most
+  // loaded one sets the batch's tail)
+  std::vector<int> order(n), branch(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto cells = [&](int i) { return (double)plans[i]->g.nx * plans[i]->g.ny * plans[i]->g.nz; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cells(a) > cells(b); });
+  std::vector<double> load(nb, 0.0);
+  for (int i : order) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    branch[i] = b;
+    load[b] += cells(i);
+  }
+  for (int k = 0; st == PPE_OK && k < n; ++k) {
+    const int i = order[k];
     ppe_plan_t P = plans[i];
     cudaStream_t saved = P->stream;
-    P->stream = bs[i % nb];
+    P->stream = bs[branch[i]];
     st = ppe_project(P, &fields[i]);
     P->stream = saved;
   }

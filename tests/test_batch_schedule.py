@@ -112,9 +112,11 @@ def test_batch_queue_of_the_uneven_batch(window, stagger, first, grain):
 def test_window_and_stagger_orders():
     dims = [(32, 32, 32), (48, 64, 32), (64, 48, 96), (96, 32, 32)]
     rho = [False] * 4
-    # one window: stage-major (every grid's stage s before any stage s + 1)
+    cells = [a * b * c for a, b, c in dims]
+    # one window: stage-major (every grid's stage s before any stage s + 1),
+    # larger grids first within a stage
     items = ppe.batch_schedule(dims, rho, window=0)[0]
-    keys = [(s, g) for g, s, _, _ in items]
+    keys = [(s, -cells[g], g) for g, s, _, _ in items]
     assert keys == sorted(keys)
     # windows of one grid staggered by more than the stage count: grid after grid
     items = ppe.batch_schedule(dims, rho, window=1, stagger=1000)[0]
@@ -122,7 +124,7 @@ def test_window_and_stagger_orders():
     assert gs == sorted(gs)
     # windows of two grids, stagger 3: grid 2's stage s sits with grids 0-1's stage s + 3
     items = ppe.batch_schedule(dims, rho, window=2, stagger=3)[0]
-    keys = [(s + 3 * (g // 2), g, s) for g, s, _, _ in items]
+    keys = [(s + 3 * (g // 2), -cells[g], g, s) for g, s, _, _ in items]
     assert keys == sorted(keys)
 
 
