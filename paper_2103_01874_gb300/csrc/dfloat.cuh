@@ -277,6 +277,33 @@ PPE_HD dd operator-(dd a, dd b) { return dd(df_sub(a.pair(), b.pair())); }
 PPE_HD dd operator-(dd a) { return dd(-a.hi, -a.lo); }
 PPE_HD dd operator*(dd a, dd b) { return dd(df_mul(a.pair(), b.pair())); }
 PPE_HD dd operator/(dd a, dd b) { return dd(df_mul(a.pair(), df_recip(b.pair()))); }
+// a b - c d (SUB) or a b + c d with one normalisation: the two TwoProds of
+// the high parts, their TwoSum, the low parts and the four cross terms summed
+// in FP32 (the error of the normalised products and sum taken together, about
+// 2^-47 relative; 19 FP32 operations against 25 for two products and a sum).
+template <bool SUB>
+PPE_HD dd dd_dot2(dd a, dd b, dd c, dd d) {
+  const float ch = SUB ? -c.hi : c.hi, cl = SUB ? -c.lo : c.lo;
+  const df p = two_prod(a.hi, b.hi);
+  const df q = two_prod(ch, d.hi);
+  const df t = two_sum(p.hi, q.hi);
+  float lo = (p.lo + q.lo) + t.lo;
+  lo = fmaf(a.hi, b.lo, lo);
+  lo = fmaf(a.lo, b.hi, lo);
+  lo = fmaf(ch, d.lo, lo);
+  lo = fmaf(cl, d.hi, lo);
+  return dd(fast_two_sum(t.hi, lo));
+}
+// a + b without the final renormalisation (the lazy add above, as a dd): the
+// high parts' TwoSum is exact, the low parts are summed in FP32; the result's
+// low part may exceed half an ulp of its high part by a few ulps, which the
+// next normalisation (dd_norm, a product, an add) absorbs.
+PPE_HD dd dd_add_lazy(dd a, dd b) {
+  const df s = two_sum(a.hi, b.hi);
+  return dd(s.hi, s.lo + (a.lo + b.lo));
+}
+PPE_HD dd dd_sub_lazy(dd a, dd b) { return dd_add_lazy(a, dd(-b.hi, -b.lo)); }
+PPE_HD dd dd_norm(dd a) { return dd(fast_two_sum(a.hi, a.lo)); }
 PPE_HD dd& operator+=(dd& a, dd b) { return a = a + b; }
 PPE_HD dd& operator-=(dd& a, dd b) { return a = a - b; }
 PPE_HD dd& operator*=(dd& a, dd b) { return a = a * b; }

@@ -22,6 +22,7 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "fastdiv.cuh"
 
 namespace ppe {
@@ -36,6 +37,10 @@ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
   r.x = a.x * b.x - a.y * b.y;
   r.y = a.x * b.y + a.y * b.x;
   return r;
+}
+// pairs: each component with one normalisation (dd_dot2)
+__device__ __forceinline__ cpx<dd> cmul(cpx<dd> a, cpx<dd> b) {
+  return {dd_dot2<true>(a.x, b.x, a.y, b.y), dd_dot2<false>(a.x, b.y, a.y, b.x)};
 }
 template <typename T>
 __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
@@ -76,7 +81,8 @@ __device__ __forceinline__ cpx<T> tw16(cpx<T> v) {
   if (m == 4) return rot<T, INV>(v);                 // -i forward
   if (m == 12) return rot<T, !INV>(v);               // +i forward
   constexpr T cr = (T)c, si = INV ? (T)s : (T)(-s);  // w = c - i s (forward)
-  return {v.x * cr - v.y * si, v.x * si + v.y * cr};
+  if constexpr (std::is_same<T, dd>::value) return {dd_dot2<true>(v.x, cr, v.y, si), dd_dot2<false>(v.x, si, v.y, cr)};
+  else return {v.x * cr - v.y * si, v.x * si + v.y * cr};
 }
 
 template <typename T, bool INV, int R> struct SmallDft;
@@ -113,6 +119,48 @@ template <typename T, bool INV> struct SmallDft<T, INV, 4> {
     v[2] = csub(a0, b0);
     v[1] = cadd(a1, b1);
     v[3] = csub(a1, b1);
+  }
+};
+
+// Pairs: the butterflies' adds are lazy (dd_add_lazy) and each output is
+// normalised once at the end, so every value leaving a small DFT is a
+// normalised pair (the larger radices are built from these).
+__device__ __forceinline__ cpx<dd> cadd_l(cpx<dd> a, cpx<dd> b) { return {dd_add_lazy(a.x, b.x), dd_add_lazy(a.y, b.y)}; }
+__device__ __forceinline__ cpx<dd> csub_l(cpx<dd> a, cpx<dd> b) { return {dd_sub_lazy(a.x, b.x), dd_sub_lazy(a.y, b.y)}; }
+__device__ __forceinline__ cpx<dd> cnorm(cpx<dd> a) { return {dd_norm(a.x), dd_norm(a.y)}; }
+
+template <bool INV> struct SmallDft<dd, INV, 2> {
+  static __device__ __forceinline__ void run(cpx<dd>* v) {
+    const cpx<dd> a = v[0], b = v[1];
+    v[0] = cnorm(cadd_l(a, b));
+    v[1] = cnorm(csub_l(a, b));
+  }
+};
+
+template <bool INV> struct SmallDft<dd, INV, 3> {
+  static __device__ __forceinline__ void run(cpx<dd>* v) {
+    constexpr dd s3 = dd(0.86602540378443864676372317075294);
+    const cpx<dd> t1 = cadd_l(v[1], v[2]);
+    // v0 - t1/2 (halving is exact on both parts)
+    const cpx<dd> h = {dd(0.5f * t1.x.hi, 0.5f * t1.x.lo), dd(0.5f * t1.y.hi, 0.5f * t1.y.lo)};
+    const cpx<dd> t2 = csub_l(v[0], h);
+    const cpx<dd> d = csub_l(v[1], v[2]);
+    const cpx<dd> t3 = {s3 * d.x, s3 * d.y};
+    const cpx<dd> r = rot<dd, INV>(t3);
+    v[0] = cnorm(cadd_l(v[0], t1));
+    v[1] = cnorm(cadd_l(t2, r));
+    v[2] = cnorm(csub_l(t2, r));
+  }
+};
+
+template <bool INV> struct SmallDft<dd, INV, 4> {
+  static __device__ __forceinline__ void run(cpx<dd>* v) {
+    const cpx<dd> a0 = cadd_l(v[0], v[2]), a1 = csub_l(v[0], v[2]);
+    const cpx<dd> b0 = cadd_l(v[1], v[3]), b1 = rot<dd, INV>(csub_l(v[1], v[3]));
+    v[0] = cnorm(cadd_l(a0, b0));
+    v[2] = cnorm(csub_l(a0, b0));
+    v[1] = cnorm(cadd_l(a1, b1));
+    v[3] = cnorm(csub_l(a1, b1));
   }
 };
 

@@ -35,6 +35,21 @@ int main() {
       std::scanf("%la %la", &h, &l);
       const df a{(float)h, (float)l};
       std::printf("%a\n", op[4] ? df2d_alu(a) : df2d(a));
+    } else if (!std::strcmp(op, "dot2sub") || !std::strcmp(op, "dot2add")) {
+      // a b -+ c d for four pairs
+      double v[8];
+      for (int i = 0; i < 8; ++i) std::scanf("%la", &v[i]);
+      const dd a((float)v[0], (float)v[1]), b((float)v[2], (float)v[3]), c((float)v[4], (float)v[5]),
+          d((float)v[6], (float)v[7]);
+      const dd r = op[4] == 's' ? dd_dot2<true>(a, b, c, d) : dd_dot2<false>(a, b, c, d);
+      std::printf("%a %a\n", (double)r.hi, (double)r.lo);
+    } else if (!std::strcmp(op, "addlazy")) {
+      // a + b + c with lazy adds, then one normalisation
+      double v[6];
+      for (int i = 0; i < 6; ++i) std::scanf("%la", &v[i]);
+      const dd a((float)v[0], (float)v[1]), b((float)v[2], (float)v[3]), c((float)v[4], (float)v[5]);
+      const dd r = dd_norm(dd_add_lazy(dd_add_lazy(a, b), c));
+      std::printf("%a %a\n", (double)r.hi, (double)r.lo);
     } else {
       double ah, al, bh, bl;
       std::scanf("%la %la %la %la", &ah, &al, &bh, &bl);

@@ -114,6 +114,51 @@ def test_pair_arithmetic(harness, op):
         assert abs(got - want) <= bound, (op, pa, pb, hi, lo)
 
 
+@pytest.mark.parametrize("op", ["dot2sub", "dot2add"])
+def test_fused_pair_dot_product(harness, op):
+    """dd_dot2 (the pair complex multiply's components): a b -+ c d of four
+    pairs, exact rationals; bounded by 2^-45 of |a b| + |c d| (products of
+    near-equal size cancel: the bound is on the operands, like the adds')."""
+    rng = random.Random(7 if op == "dot2sub" else 8)
+    lines, args = [], []
+    for _ in range(1500):
+        xs = [rng.uniform(-1e3, 1e3) for _ in range(4)]
+        if rng.random() < 0.3:  # a b close to c d (or to -c d)
+            xs[2] = xs[0] * (1 + rng.uniform(-1e-6, 1e-6))
+            xs[3] = (xs[1] if op == "dot2sub" else -xs[1]) * (1 + rng.uniform(-1e-6, 1e-6))
+        ps = [harness_pair(x) for x in xs]
+        args.append(ps)
+        lines.append(op + " " + " ".join(f"{p[0].hex()} {p[1].hex()}" for p in ps))
+    out = harness(lines)
+    for ps, line in zip(args, out):
+        hi, lo = (float.fromhex(t) for t in line.split())
+        A, B, C, D = (Q(p[0]) + Q(p[1]) for p in ps)
+        want = A * B - C * D if op == "dot2sub" else A * B + C * D
+        got = Q(hi) + Q(lo)
+        assert abs(got - want) <= Q(2) ** -45 * (abs(A * B) + abs(C * D)), (op, ps, hi, lo)
+        assert abs(Q(lo)) <= Q(2) ** -23 * abs(Q(hi)) or hi == 0.0, "normalised"
+
+
+def test_lazy_adds_then_normalise(harness):
+    """Two lazy adds (no renormalisation between) and one dd_norm: the sum to
+    2^-45 of the operands' magnitudes, and a normalised result."""
+    rng = random.Random(11)
+    lines, args = [], []
+    for _ in range(1500):
+        xs = [rng.uniform(-1e4, 1e4) for _ in range(3)]
+        if rng.random() < 0.3:
+            xs[1] = -xs[0] * (1 + rng.uniform(-1e-6, 1e-6))
+        ps = [harness_pair(x) for x in xs]
+        args.append(ps)
+        lines.append("addlazy " + " ".join(f"{p[0].hex()} {p[1].hex()}" for p in ps))
+    out = harness(lines)
+    for ps, line in zip(args, out):
+        hi, lo = (float.fromhex(t) for t in line.split())
+        A, B, C = (Q(p[0]) + Q(p[1]) for p in ps)
+        got = Q(hi) + Q(lo)
+        assert abs(got - (A + B + C)) <= Q(2) ** -45 * (abs(A) + abs(B) + abs(C)), (ps, hi, lo)
+
+
 @pytest.mark.parametrize("d", [1, 2, 3, 5, 7, 8, 9, 12, 16, 24, 25, 48, 96, 128, 129, 193, 255, 256, 257,
                                384, 385, 513, 1025, 65536, 65537, 1 << 20, (1 << 20) + 3])
 def test_fastdiv_exact(harness, d):
