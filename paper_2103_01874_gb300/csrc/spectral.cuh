@@ -662,10 +662,23 @@ __device__ __forceinline__ void ydct_body(GridDev g, cpx<T>* spec, RadixPlan rp,
     const cpx<T> vk = V[k * tky + c], vr = V[r * tky + c];
     const cpx<T> wk = wq[k], wr = wq[r];
     const cpx<T> wkc = {wk.x, -wk.y}, wrc = {wr.x, -wr.y};
-    const cpx<T> t1 = cmul(wk, vk), t2c = cmul(wkc, vr);
-    const cpx<T> xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
-    const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
-    const cpx<T> xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
+    cpx<T> xk, xr;
+    if constexpr (std::is_same<T, dd>::value) {
+      // pairs: X_k = (w_k V_k + conj(w_k) V_r)/2 and X_r = (w_r V_r + conj(w_r) V_k)/2
+      // share the sums V_k + V_r and the differences, so that each component
+      // is half of one two-term dot product (w = a + i b):
+      // Re X_k = (a (Re V_k + Re V_r) + b (Im V_r - Im V_k))/2, and likewise
+      const dd s1 = dd_add_lazy(vk.x, vr.x), s2 = dd_add_lazy(vk.y, vr.y);
+      const dd d1 = dd_sub_lazy(vr.y, vk.y), d2 = dd_sub_lazy(vk.x, vr.x);
+      auto half = [](dd v) { return dd(0.5f * v.hi, 0.5f * v.lo); };
+      xk = {half(dd_dot2<false>(wk.x, s1, wk.y, d1)), half(dd_dot2<false>(wk.x, s2, wk.y, d2))};
+      xr = {half(dd_dot2<true>(wr.x, s1, wr.y, d1)), half(dd_dot2<true>(wr.x, s2, wr.y, d2))};
+    } else {
+      const cpx<T> t1 = cmul(wk, vk), t2c = cmul(wkc, vr);
+      xk = {(T)0.5 * (t1.x + t2c.x), (T)0.5 * (t1.y + t2c.y)};
+      const cpx<T> t3 = cmul(wr, vr), t4 = cmul(wrc, vk);
+      xr = {(T)0.5 * (t3.x + t4.x), (T)0.5 * (t3.y + t4.y)};
+    }
     const T sk = inv_n / (lxz + lam_y[k]), sr = inv_n / (lxz + lam_y[r]);
     const cpx<T> pk = {xk.x * sk, xk.y * sk}, pr = {xr.x * sr, xr.y * sr};
     // V'_k = conj(w_k)(P_k - i P_r), V'_r = conj(w_r)(P_r - i P_k);  -i z = (z.y, -z.x)
