@@ -38,8 +38,14 @@ __device__ __forceinline__ cpx<T> ld_tw(const cpx<T>* tw, int t) {
 // log2 of a power of two
 __device__ __forceinline__ int ilog2_dev(int v) { return __ffs(v) - 1; }
 
-// Transform with the compile-time-length passes when N > 0 (FP32 common
-// lengths), else with the run-time-length ones.  MAXR matches radix_plan().
+// FP32 and pair passes have compile-time-length instances (register-staged
+// for powers of two); FP64 passes run on run-time radix plans
+template <typename T>
+struct has_ct_lengths : std::integral_constant<bool, sizeof(T) == 4 || std::is_same<T, dd>::value> {};
+
+// Transform with the compile-time-length passes when N > 0 (FP32 and pair
+// lengths; radices up to 16 in FP32 and 8 in pairs, which measured faster at
+// their register counts), else with the run-time-length ones (as radix_plan()).
 template <typename T, bool INV, int N, int TWS>
 __device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int nl_log2, const RadixPlan& rp, int ls, int es,
                                           const cpx<T>* __restrict__ tw) {
@@ -60,10 +66,6 @@ __device__ __forceinline__ T rcp_of(T x) {
   else return __frcp_rn(x);
 }
 
-// FP32 and pair passes have compile-time-length instances (register-staged
-// for powers of two); FP64 passes run on run-time radix plans
-template <typename T>
-struct has_ct_lengths : std::integral_constant<bool, sizeof(T) == 4 || std::is_same<T, dd>::value> {};
 
 template <typename T, typename F>
 cudaError_t with_len(int n, F&& f) {
