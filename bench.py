@@ -587,8 +587,16 @@ def run_batched(args, dev):
     # grid tuned once: spectral schedule by the whole projection's time, then
     # the x-line tile; the others of its size class take the cached result)
     ms_default = time_batch(form=ppe.BATCH_GRAPH)
+    defaults = [pl.get_tuning() for pl, _ in items32]
     tuned = tune_plans(items32, {k: autotune.SEARCH[k] for k in ("spectral", "y_solve", "x_lines")}, stream)
     ms_graph = time_batch(form=ppe.BATCH_GRAPH)
+    # the per-plan choices were timed on each grid alone: the batch keeps them
+    # only if the whole batch runs faster with them
+    tuned["kept"] = ms_graph <= ms_default
+    if not tuned["kept"]:
+        for (pl, _), t in zip(items32, defaults):
+            pl.set_tuning(**t)
+        ms_graph = ms_default
     worst = max(pl.info(allow_not_converged=True).rel_residual for pl, _ in items32)
     persistent_wins = ms_pers is not None and ms_pers <= ms_graph
     ms_batch = ms_pers if persistent_wins else ms_graph
