@@ -148,7 +148,7 @@ cudaError_t launch_vc_correct(const GridDev& g, const double* u, const double* v
                               double2* part, double* p_out, double* u_out, double* v_out, double* w_out,
                               cudaStream_t st);
 
-// ---- launchers (k_spectral.cu) ----
+// ---- launchers (spectral.cuh, instantiated in k_spectral_f32.cu, k_spectral_f64.cu, k_spectral_dd.cu) ----
 template <typename T>
 cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn& in, DevScalars* sc,
                         int sweep_slot, df* fdf, const df* pdf, cpx<T>* spec, const RadixPlan& rp_half,
