@@ -25,6 +25,7 @@
 // it back, k_xfwd) and/or as FP64.
 #include "dfloat.cuh"
 #include "ppe_internal.h"
+#include "pdl.cuh"
 #include "stencil.cuh"
 #include "rhs.cuh"
 
@@ -37,6 +38,7 @@ namespace ppe {
 template <int CPT, int RULE, bool PROJ>
 __global__ void __launch_bounds__(kRhsThreads, (CPT <= 2) ? 3 : (CPT == 4 ? 2 : 1))
     k_rhs_march(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int tj, int kc) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int ntile = (ny + tj - 1) / tj;
@@ -303,6 +305,7 @@ __global__ void k_finish_sums(GridDev g, DevScalars* sc) { finish_sums(sc, g); }
 template <int S, int RULE, bool PROJ>
 __global__ void __launch_bounds__(kRhsThreads, (S <= 2) ? 3 : (S == 4 ? 2 : 1))
     k_rhs_stack(GridDev g, StencilIn in, DevScalars* sc, RhsOut out, int kc) {
+  pdl_enter();
   rhs_stack_tile<S, RULE, PROJ>(g, in, sc, out, kc, blockIdx.x);
 }
 
@@ -341,7 +344,7 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
   if (!proj && !f64) return cudaErrorInvalidValue;
   if (g.nx <= kRhsThreads) {
     // column-stack form: tj is the stack height S
-    auto go = [&](auto kernel) { kernel<<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, kc); };
+    auto go = [&](auto kernel) { launch_pdl(kernel, grid, kRhsThreads, sm, st, g, in, sc, o, kc); };
 #define PPE_STACK_CASE(C)                                                        \
     if (tj == C) {                                                               \
       if (in.face_rule == 0) {                                                   \
@@ -359,7 +362,7 @@ cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, do
   }
   const int ncol = tj * g.nx;
   const int cpt = ncol <= kRhsThreads ? 1 : ncol <= 2 * kRhsThreads ? 2 : ncol <= 4 * kRhsThreads ? 4 : 8;
-  auto go = [&](auto kernel) { kernel<<<grid, kRhsThreads, sm, st>>>(g, in, sc, o, tj, kc); };
+  auto go = [&](auto kernel) { launch_pdl(kernel, grid, kRhsThreads, sm, st, g, in, sc, o, tj, kc); };
   // instance table: [cpt][rule][proj]
 #define PPE_RHS_CASE(C)                                                        \
   if (cpt == C) {                                                              \

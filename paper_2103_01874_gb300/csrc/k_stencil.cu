@@ -2,6 +2,7 @@
 // the velocity correction of Eq. (33), and the device-side refinement control.
 #include "dfloat.cuh"
 #include "ppe_internal.h"
+#include "pdl.cuh"
 #include "stencil.cuh"
 #include "correct.cuh"
 
@@ -9,10 +10,12 @@ namespace ppe {
 
 __global__ void k_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, double* out_p,
                                double* out_u, double* out_v, double* out_w) {
+  pdl_enter();
   if (threadIdx.x == 0) init_scalars(sc, rho0, tol, keep_rho0, out_p, out_u, out_v, out_w);
 }
 
 __global__ void __launch_bounds__(256) k_rho_min(const double* __restrict__ rho, size_t n, DevScalars* sc) {
+  pdl_enter();
   rho_min_body(rho, n, sc, blockIdx.x, gridDim.x);
 }
 
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(256) k_df_to_d(const df* __restrict__ a, doubl
 
 __global__ void k_refine_check(DevScalars* sc, int smax, int off, cudaGraphConditionalHandle handle,
                                int use_handle) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   const int cont = refine_decide(sc, smax, off);
   if (use_handle) cudaGraphSetConditional(handle, cont);
@@ -140,10 +144,12 @@ __global__ void __launch_bounds__(256, 4) k_correct_check(GridDev g, const df* _
                                                        const df* __restrict__ vpre, const df* __restrict__ wpre,
                                                        const df* __restrict__ pdf, const df* __restrict__ fdf,
                                                        DevScalars* sc) {
+  pdl_enter();
   correct_check_tile(g, upre, vpre, wpre, pdf, fdf, sc, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_make_const(GridDev g, DevScalars* sc, double dt) {
+  pdl_enter();
   if (threadIdx.x == 0) sc->K = make_const(g, read_rho0(sc), dt);
 }
 
@@ -185,6 +191,25 @@ unsigned grid_for(size_t total, size_t cap) {
   if (b == 0) b = 1;
   return (unsigned)b;
 }
+// One wave of 256-thread CTAs: the SMs times the CTAs of `kernel` resident per
+// SM (taken once per kernel).  The grid-stride correction kernels launched
+// this way keep every resident slot busy to the end; several waves of short
+// CTAs measured slower (230 against 216 us at 256^3 for the correction check:
+// the slots refill unevenly between waves).
+template <auto kernel>
+size_t one_wave() {
+  static const size_t ctas = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      return (size_t)152 * 4;
+    }
+    return (size_t)sms * (size_t)per_sm;
+  }();
+  return ctas;
+}
 }  // namespace
 
 cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_g, const double* comp_l,
@@ -197,7 +222,7 @@ cudaError_t launch_div_constraint(size_t n, const double* C, const double* comp_
 
 cudaError_t launch_init_scalars(DevScalars* sc, double rho0, double tol, int keep_rho0, cudaStream_t st,
                                 double* out_p, double* out_u, double* out_v, double* out_w) {
-  k_init_scalars<<<1, 32, 0, st>>>(sc, rho0, tol, keep_rho0, out_p, out_u, out_v, out_w);
+  launch_pdl(k_init_scalars, 1, 32, 0, st, sc, rho0, tol, keep_rho0, out_p, out_u, out_v, out_w);
   return cudaGetLastError();
 }
 
@@ -207,12 +232,12 @@ cudaError_t launch_set_rho0(DevScalars* sc, double rho0, cudaStream_t st) {
 }
 
 cudaError_t launch_make_const(const GridDev& g, DevScalars* sc, double dt, cudaStream_t st) {
-  k_make_const<<<1, 32, 0, st>>>(g, sc, dt);
+  launch_pdl(k_make_const, 1, 32, 0, st, g, sc, dt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rho_min(const double* rho, size_t n, DevScalars* sc, cudaStream_t st) {
-  k_rho_min<<<grid_for(n, 152 * 8), 256, 0, st>>>(rho, n, sc);
+  launch_pdl(k_rho_min, grid_for(n, 152 * 8), 256, 0, st, rho, n, sc);
   return cudaGetLastError();
 }
 
@@ -220,7 +245,7 @@ cudaError_t launch_correct_pre(const GridDev& g, double dt, const df* upre, cons
                                const df* pdf, double* p64, const DevScalars* sc, double* u_out, double* v_out,
                                double* w_out, cudaStream_t st) {
   const size_t total = (size_t)g.nz * (g.ny + 1) * g.nx;
-  k_correct_pre<<<grid_for(total, (size_t)152 * 64), 256, 0, st>>>(g, dt, upre, vpre, wpre, pdf, p64, sc, u_out,
+  k_correct_pre<<<grid_for(total, one_wave<k_correct_pre>()), 256, 0, st>>>(g, dt, upre, vpre, wpre, pdf, p64, sc, u_out,
                                                                    v_out, w_out);
   return cudaGetLastError();
 }
@@ -228,14 +253,14 @@ cudaError_t launch_correct_pre(const GridDev& g, double dt, const df* upre, cons
 cudaError_t launch_correct_full(const GridDev& g, const StencilIn& in, const DevScalars* sc, double* u_out,
                                 double* v_out, double* w_out, cudaStream_t st) {
   const size_t total = (size_t)g.nz * (g.ny + 1) * g.nx;
-  k_correct_full<<<grid_for(total, (size_t)152 * 64), 256, 0, st>>>(g, in, sc, u_out, v_out, w_out);
+  k_correct_full<<<grid_for(total, one_wave<k_correct_full>()), 256, 0, st>>>(g, in, sc, u_out, v_out, w_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_correct_check(const GridDev& g, const df* upre, const df* vpre, const df* wpre, const df* pdf,
                                  const df* fdf, DevScalars* sc, cudaStream_t st) {
   const size_t total = (size_t)g.nz * (g.ny + 1) * g.nx;
-  k_correct_check<<<grid_for(total, (size_t)152 * 64), 256, 0, st>>>(g, upre, vpre, wpre, pdf, fdf, sc);
+  launch_pdl(k_correct_check, grid_for(total, one_wave<k_correct_check>()), 256, 0, st, g, upre, vpre, wpre, pdf, fdf, sc);
   return cudaGetLastError();
 }
 
@@ -246,7 +271,7 @@ cudaError_t launch_df_to_d(const df* a, double* out, size_t n, cudaStream_t st) 
 
 cudaError_t launch_refine_check(DevScalars* sc, int smax, int off, cudaGraphConditionalHandle handle,
                                 int use_handle, cudaStream_t st) {
-  k_refine_check<<<1, 32, 0, st>>>(sc, smax, off, handle, use_handle);
+  launch_pdl(k_refine_check, 1, 32, 0, st, sc, smax, off, handle, use_handle);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 #include "async.cuh"
 #include "dfloat.cuh"
 #include "ppe_internal.h"
+#include "pdl.cuh"
 #include "stencil.cuh"
 
 namespace ppe {
@@ -420,6 +421,7 @@ template <int SRC, int M, bool OPEN, bool PL = false>
 __global__ void __launch_bounds__(256) k_xfwd_rg(GridDev g, StencilIn in, DevScalars* sc, int slot, df* fdf,
                                                  const df* __restrict__ pdf, cpx<float>* spec,
                                                  const cpx<float>* __restrict__ tw, int L) {
+  pdl_enter();
   xfwd_rg_body<SRC, M, OPEN, PL>(g, in, sc, slot, fdf, pdf, spec, tw, L, blockIdx.x, gridDim.x);
 }
 
@@ -495,6 +497,7 @@ __device__ __forceinline__ void zfft_rg_body(GridDev g, cpx<T>* spec, const cpx<
 template <typename T, bool INV, int N>
 __global__ void __launch_bounds__(256) k_zfft_rg(GridDev g, cpx<T>* spec, const cpx<T>* __restrict__ tw, int L,
                                                  const DevScalars* sc, DevScalars* fin) {
+  pdl_enter();
   zfft_rg_body<T, INV, N>(g, spec, tw, L, sc, fin, blockIdx.x, gridDim.x);
 }
 
@@ -786,6 +789,7 @@ __global__ void __launch_bounds__(256, 4) k_ydct_rg(GridDev g, cpx<T>* spec, con
                                                  const cpx<T>* __restrict__ wq, const T* __restrict__ lam_x,
                                                  const T* __restrict__ lam_y, const T* __restrict__ lam_z, int L,
                                                  const DevScalars* zsc) {
+  pdl_enter();
   ydct_rg_body<T, N>(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc, blockIdx.x, gridDim.x);
 }
 
@@ -888,6 +892,7 @@ static __global__ void __launch_bounds__(256, 4) k_ydct256(GridDev g, cpx<float>
                                                   const cpx<float>* __restrict__ wq, const float* __restrict__ lam_x,
                                                   const float* __restrict__ lam_y, const float* __restrict__ lam_z,
                                                   int L, const DevScalars* zsc) {
+  pdl_enter();
   ydct256_body(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc, blockIdx.x, gridDim.x);
 }
 
@@ -1113,6 +1118,7 @@ template <int MODE, int M, bool PL = false>
 __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
                                                  double scale, const cpx<float>* __restrict__ tw, int L,
                                                  const DevScalars* sc, DevScalars* psc) {
+  pdl_enter();
   xinv_rg_body<MODE, M, PL>(g, spec, p, pdf, scale, tw, L, sc, psc, blockIdx.x, gridDim.x);
 }
 
@@ -1196,7 +1202,7 @@ cudaError_t launch_xfwd(int src, bool do_fft, const GridDev& g, const StencilIn&
         auto go = [&](auto kernel) -> cudaError_t {
           cudaError_t e2 = allow_smem(kernel, smr);
           if (e2 != cudaSuccess) return e2;
-          kernel<<<gr, L * (N / 16), smr, st>>>(g, in, sc, slot, fdf, pdf, (cpx<float>*)spec, (const cpx<float>*)tw, L);
+          launch_pdl(kernel, gr, L * (N / 16), smr, st, g, in, sc, slot, fdf, pdf, (cpx<float>*)spec, (const cpx<float>*)tw, L);
           return cudaGetLastError();
         };
         if (g.spec_planes) {
@@ -1250,10 +1256,10 @@ cudaError_t launch_zfft(bool inverse, const GridDev& g, cpx<T>* spec, const Radi
       const size_t smr = rg_smem<T>(N, L);
       if (inverse) {
         if ((e = allow_smem(k_zfft_rg<T, true, N>, smr)) != cudaSuccess) return e;
-        k_zfft_rg<T, true, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, L, sc, fin);
+        launch_pdl(k_zfft_rg<T, true, N>, gr, L * (N / 16), smr, st, g, spec, tw, L, sc, fin);
       } else {
         if ((e = allow_smem(k_zfft_rg<T, false, N>, smr)) != cudaSuccess) return e;
-        k_zfft_rg<T, false, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, L, sc, fin);
+        launch_pdl(k_zfft_rg<T, false, N>, gr, L * (N / 16), smr, st, g, spec, tw, L, sc, fin);
       }
       return cudaGetLastError();
     }
@@ -1295,14 +1301,14 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
       if constexpr (N == 256 && sizeof(T) == 4) {
         cudaError_t e = allow_smem(k_ydct256, smr);
         if (e != cudaSuccess) return e;
-        k_ydct256<<<gr, L * (N / 16), smr, st>>>(g, (cpx<float>*)spec, (const cpx<float>*)tw,
+        launch_pdl(k_ydct256, gr, L * (N / 16), smr, st, g, (cpx<float>*)spec, (const cpx<float>*)tw,
                                                  (const cpx<float>*)wq, (const float*)lam_x, (const float*)lam_y,
                                                  (const float*)lam_z, L, zsc);
         return cudaGetLastError();
       }
       cudaError_t e = allow_smem(k_ydct_rg<T, N>, smr);
       if (e != cudaSuccess) return e;
-      k_ydct_rg<T, N><<<gr, L * (N / 16), smr, st>>>(g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc);
+      launch_pdl(k_ydct_rg<T, N>, gr, L * (N / 16), smr, st, g, spec, tw, wq, lam_x, lam_y, lam_z, L, zsc);
       return cudaGetLastError();
     }
     cudaError_t e = allow_smem(k_ydct<T, N>, sm);
@@ -1332,7 +1338,7 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
       auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e2 = allow_smem(kernel, smr);
         if (e2 != cudaSuccess) return e2;
-        kernel<<<gr, L * (N / 16), smr, st>>>(g, (const cpx<float>*)spec, p, pdf, scale, (const cpx<float>*)tw, L,
+        launch_pdl(kernel, gr, L * (N / 16), smr, st, g, (const cpx<float>*)spec, p, pdf, scale, (const cpx<float>*)tw, L,
                                                sc, psc);
         return cudaGetLastError();
       };
