@@ -52,3 +52,25 @@ def test_more_sweeps_do_not_drift(case):
     for key in ("u", "v", "w"):
         assert _err(r4[key], ref[key]) <= 1e-13, key
         assert _err(r4[key], r2[key]) <= 1e-13, key
+
+
+# wall-normal lengths with their own FP32 y-pass code: 256 (the two-pass,
+# register-resident form), 128 (the general register-staged form), 48 (the
+# shared-memory form for lengths that are not powers of two)
+@pytest.mark.parametrize("shape", [(32, 256, 48), (64, 256, 64), (128, 256, 32), (64, 128, 48), (64, 48, 32)])
+def test_one_sweep_residual_bound(shape):
+    """Exactly one sweep from the FP32 solve: the relative residual is at most
+    3e-12 and p, u, v, w are within 1e-11 of the oracle.  With the FP32 solve
+    accurate to ~5e-7 in the residual, one pair sweep leaves ~1e-12; a y pass
+    whose FP32 rounding is several times worse (the two halves of each cosine
+    pair rounded differently, say) leaves 5e-12 to 2e-11 here and fails."""
+    from _gpu_util import project_gpu
+    nx, ny, nz = shape
+    fl = fields.make_fields(nx, ny, nz, seed=sum(shape), recipe="single", width=2.0)
+    ref = O.project_fields(fl)
+    res, info = project_gpu(fl, precision=ppe.FP32_REFINE, refine_tol=0.0, max_sweeps=1)
+    assert info.sweeps == 1
+    assert info.rel_residual <= 3e-12, (shape, info.rel_residual)
+    for key in ("u", "v", "w"):
+        assert _err(res[key], ref[key]) <= 1e-11, (shape, key)
+    assert np.abs(res["p"] - ref["p"]).max() <= 1e-11 * np.abs(ref["p"]).max(), shape
