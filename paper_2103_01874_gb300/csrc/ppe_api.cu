@@ -44,6 +44,9 @@ struct ppe_plan_s {
   int tj, kc;         // right-hand-side kernel: lines per tile, planes per chunk
   df* fdf;            // FP32_REFINE: right-hand side as pairs, kept for the residual
   df* pdf;            // FP32_REFINE: pressure as pairs during the refinement
+  float* p32;         // FP32_REFINE, register-staged x passes, (nx/2) nz a power of two, max_sweeps >= 1:
+                      // ppe_project's first-solve p in FP32 (a pair with a zero low part), read by the
+                      // first sweep's residual and accumulation
   df* upre;           // explicitly split velocity u_pre on x faces (ppe_project)
   df* vpre;           //   ... on y faces
   df* wpre;           //   ... on z faces
@@ -415,7 +418,8 @@ StencilIn make_in(ppe_plan_t P, const double* u, const double* v, const double* 
 // and the next solve's zero mode takes minus that sum (the refinement keeps p
 // zero-mean); off where the solve is a preconditioner, not a pressure.
 template <typename T>
-ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded, bool psum = true) {
+ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded, bool psum = true,
+                      float* p32 = nullptr) {
   DevScalars* psc = (psum && mode != XI_F64) ? P->sc : nullptr;
   const DevScalars* sc = guarded ? P->sc : nullptr;
   cpx<T>* spec = (cpx<T>*)P->spec;
@@ -438,7 +442,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
     }
     PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
                launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
-                              psc, P->stream));
+                              psc, P->stream, p32));
     return PPE_OK;
   }
   PPE_LAUNCH(P, K_ZFFT_FWD,
@@ -458,7 +462,7 @@ ppe_status solve_tail(ppe_plan_t P, int mode, double* p64, df* pdf, bool guarded
              launch_zfft<T>(true, P->gd, spec, P->rp_z, (const cpx<T>*)P->tw_z, P->tkx, sc, nullptr, P->stream));
   PPE_LAUNCH(P, mode == XI_DF_ACC ? K_XINV_ACC : K_XINV,
              launch_xinv<T>(mode, P->gd, spec, p64, pdf, scale, P->rp_half, (const cpx<T>*)P->tw_x, P->lpb, sc,
-                            psc, P->stream));
+                            psc, P->stream, p32));
   return PPE_OK;
 }
 
@@ -480,9 +484,11 @@ ppe_status with_fp64_type(ppe_plan_t P, F&& f) {
 //               after the last correction needs no separate residual pass.
 enum RefMode { REF_SOLVE = 0, REF_PROJECT = 1 };
 
-ppe_status resid_fwd(ppe_plan_t P) {
+// p0f: the first solve's p in FP32 (read at the first sweep), or NULL
+ppe_status resid_fwd(ppe_plan_t P, const float* p0f) {
   StencilIn in;
   memset(&in, 0, sizeof(in));
+  in.p0f = p0f;
   PPE_LAUNCH(P, K_XFWD_RESID, launch_xfwd<float>(SRC_RESID, true, P->gd, in, P->sc, -1, P->fdf, P->pdf,
                                                  (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x,
                                                  P->lpb, P->stream));
@@ -490,7 +496,7 @@ ppe_status resid_fwd(ppe_plan_t P) {
 }
 
 ppe_status refine_probe(ppe_plan_t P, cudaGraphConditionalHandle h, int use_handle) {
-  ppe_status s = resid_fwd(P);
+  ppe_status s = resid_fwd(P, nullptr);
   if (s != PPE_OK) return s;
   PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, 0, h, use_handle, P->stream));
   return PPE_OK;
@@ -502,8 +508,8 @@ ppe_status refine_body(ppe_plan_t P, int mode, cudaGraphConditionalHandle h, int
     if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) return s;
     return refine_probe(P, h, use_handle);
   }
-  if ((s = resid_fwd(P)) != PPE_OK) return s;
-  if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false)) != PPE_OK) return s;
+  if ((s = resid_fwd(P, P->p32)) != PPE_OK) return s;
+  if ((s = solve_tail<float>(P, XI_DF_ACC, nullptr, P->pdf, false, true, P->p32)) != PPE_OK) return s;
   PPE_LAUNCH(P, K_CORRECT, launch_correct_check(P->gd, P->upre, P->vpre, P->wpre, P->pdf, P->fdf, P->sc, P->stream));
   PPE_LAUNCH(P, K_CHECK, launch_refine_check(P->sc, P->opt.max_sweeps, 1, h, use_handle, P->stream));
   return PPE_OK;
@@ -753,6 +759,16 @@ ppe_status refine(ppe_plan_t P, int mode) {
   return s;
 }
 
+// Plans whose ppe_project keeps the first solve's p in FP32 (XI_F32): the FP32
+// form with at least one sweep, register-staged x passes (nx/2 a power of two
+// with a compiled length, 16 .. 256) and an exact inverse-transform scaling
+// ((nx/2) nz a power of two).
+bool p32_ok(const ppe_grid& g, const ppe_options& o) {
+  const unsigned m = (unsigned)(g.nx / 2), s = m * (unsigned)g.nz;
+  return o.precision == PPE_FP32_REFINE && o.max_sweeps >= 1 && m >= 16 && m <= 256 && (m & (m - 1u)) == 0u &&
+         (s & (s - 1u)) == 0u;
+}
+
 // Tile sizes of the right-hand-side kernel: largest tj in {8, 4, 2, 1} whose
 // shared memory lets two CTAs share an SM, else one.
 void choose_rhs_tiles(ppe_plan_t P) {
@@ -793,6 +809,7 @@ size_t ppe_workspace_bytes(const ppe_grid* g, const ppe_options* opt) {
   const size_t nxh = g->nx / 2 + 1;
   size_t b = cb * nxh * g->ny * g->nz + cb * (g->nx + g->nz) + sizeof(DevScalars);
   b += (fp32 ? 16 : 8) * n;                                             // f (and p) as pairs
+  if (opt && p32_ok(*g, *opt)) b += 4 * n;                              // the first solve's p in FP32
   b += 8 * (2 * n + (size_t)g->nx * (g->ny + 1) * g->nz);               // u_pre, v_pre, w_pre
   b += (fp32 ? 4 : 8) * nxh * g->nz * (size_t)g->ny + 8 * nxh * g->nz;  // upper bound of the tables
   b += 48 * (size_t)g->ny * g->nz;                                       // per-CTA partial sums
@@ -869,11 +886,13 @@ ppe_status ppe_plan(ppe_plan_t* out, const ppe_grid* g, const ppe_options* opt, 
   const size_t ncell = (size_t)g->nx * g->ny * g->nz, nvf = (size_t)g->nx * (g->ny + 1) * g->nz;
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->fdf, sizeof(df) * ncell));
   if (s == PPE_OK && P->fp32) s = alloc_status(cudaMalloc((void**)&P->pdf, sizeof(df) * ncell));
+  if (s == PPE_OK && p32_ok(P->g, o)) s = alloc_status(cudaMalloc((void**)&P->p32, sizeof(float) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->upre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->vpre, sizeof(df) * nvf));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->wpre, sizeof(df) * ncell));
   if (s == PPE_OK) s = alloc_status(cudaMalloc((void**)&P->rhs_part, 3 * sizeof(double2) * g->ny * g->nz));
   P->workspace = nspec * P->cplx_bytes + sizeof(DevScalars) + (P->fp32 ? 2 : 1) * sizeof(df) * ncell +
+                 (P->p32 ? sizeof(float) * ncell : 0) +
                  sizeof(df) * (2 * ncell + nvf) + P->cplx_bytes * (g->nx + g->nz) +
                  3 * sizeof(double2) * g->ny * g->nz;
   choose_rhs_tiles(P);
@@ -964,6 +983,7 @@ void ppe_destroy(ppe_plan_t P) {
   cudaFree(P->pcg_part);
   if (P->pcg_exec) cudaGraphExecDestroy(P->pcg_exec);
   cudaFree(P->pdf);
+  cudaFree(P->p32);
   cudaFree(P->upre);
   cudaFree(P->vpre);
   cudaFree(P->wpre);
@@ -1148,7 +1168,9 @@ ppe_status ppe_project(ppe_plan_t P, const ppe_fields* F) {
     PPE_LAUNCH(P, K_XFWD_F, launch_xfwd<float>(SRC_FDF, true, P->gd, in, P->sc, 0, P->fdf, nullptr,
                                                (cpx<float>*)P->spec, P->rp_half, (const cpx<float>*)P->tw_x, P->lpb,
                                                P->stream));
-    if ((s = solve_tail<float>(P, XI_DF, nullptr, P->pdf, false)) != PPE_OK) return s;
+    // the first solve's p: in FP32 where the first sweep reads it so (p32), else as pairs
+    if ((s = solve_tail<float>(P, P->p32 ? XI_F32 : XI_DF, nullptr, P->pdf, false, true, P->p32)) != PPE_OK)
+      return s;
     if ((s = refine(P, REF_PROJECT)) != PPE_OK) return s;
   } else {
     PPE_LAUNCH(P, K_RHS, launch_rhs(P->gd, in, P->sc, F->f, P->fdf, P->upre, P->vpre, P->wpre, P->tj, P->kc,

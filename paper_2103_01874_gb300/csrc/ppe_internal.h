@@ -99,13 +99,15 @@ struct StencilIn {
   const double *u, *v, *w, *S, *rho, *pn, *pnm1;
   const double* f;   // SRC_F / SRC_RESID: the right-hand side
   const double* p;   // SRC_RESID / correction: the pressure
+  const float* p0f;  // SRC_RESID (FP32 register-staged pass): the first solve's p in FP32, read at the
+                     // first sweep (sc->iter == 1) in place of the pairs; NULL: always the pairs
   double inv_dt;
   double dt;
   int face_rule;     // 0 arithmetic, 1 harmonic
 };
 
 enum XSource { SRC_F = 1, SRC_RESID = 2, SRC_FDF = 3 };
-enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2 };
+enum XInvMode { XI_F64 = 0, XI_DF = 1, XI_DF_ACC = 2, XI_F32 = 3 };
 
 // ---- launchers (k_rhs.cu) ----
 cudaError_t launch_rhs(const GridDev& g, const StencilIn& in, DevScalars* sc, double* f64, df* fdf, df* upre,
@@ -166,11 +168,15 @@ template <typename T>
 cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, const cpx<T>* tw, const cpx<T>* wq,
                         const T* lam_x, const T* lam_y, const T* lam_z, int tky, const DevScalars* zsc,
                         cudaStream_t st);
-// psc non-NULL (XI_DF, XI_DF_ACC): the per-CTA sums of the p written go to psc->part[2 ny nz ..]
+// psc non-NULL (XI_DF, XI_DF_ACC, XI_F32): the per-CTA sums of the p written go to psc->part[2 ny nz ..].
+// XI_F32 (FP32 register-staged pass: nx/2 in 16 .. 256 a power of two, (nx/2) nz a power of two, so that
+// the 1/((nx/2) nz) scaling is exact and the pair the XI_DF mode would store has a zero low part): p into
+// p32 as FP32.  XI_DF_ACC with p32 non-NULL adds the correction to that FP32 p at the first sweep
+// (psc->iter == 1), to the pairs later.
 template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp_half, const cpx<T>* tw_x, int lpb, const DevScalars* sc,
-                        DevScalars* psc, cudaStream_t st);
+                        DevScalars* psc, cudaStream_t st, float* p32 = nullptr);
 template <typename T>
 size_t xfwd_smem(int nx, int lpb);
 template <typename T>

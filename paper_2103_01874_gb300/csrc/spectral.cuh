@@ -348,6 +348,15 @@ __device__ __forceinline__ void xfwd_rg_body(GridDev g, StencilIn in, DevScalars
     const float4* pym4 = reinterpret_cast<const float4*>(pdf + (has_ym ? c0 - nx : c0));
     const float4* pyp4 = reinterpret_cast<const float4*>(pdf + (has_yp ? c0 + nx : c0));
     const float4* f4 = reinterpret_cast<const float4*>(fdf + c0);
+    // the first sweep may read the first solve's p in FP32 (a pair with a zero
+    // low part: the same values)
+    const bool p0f = in.p0f != nullptr && sc->iter == 1;
+    const float* ql = p0f ? in.p0f + c0 : nullptr;
+    const float2* qc2 = reinterpret_cast<const float2*>(ql);
+    const float2* qzm2 = reinterpret_cast<const float2*>(p0f ? in.p0f + (k == 0 ? c0 + (nzu - 1) * plane : c0 - plane) : nullptr);
+    const float2* qzp2 = reinterpret_cast<const float2*>(p0f ? in.p0f + (k + 1 == nzu ? c0 - (nzu - 1) * plane : c0 + plane) : nullptr);
+    const float2* qym2 = reinterpret_cast<const float2*>(p0f ? in.p0f + (has_ym ? c0 - nx : c0) : nullptr);
+    const float2* qyp2 = reinterpret_cast<const float2*>(p0f ? in.p0f + (has_yp ? c0 + nx : c0) : nullptr);
     auto res = [&](df pc, df pxm, df pxp, df pym, df pyp, df pzm, df pzp, df fv) {
       const df p2 = df_ldexp2(pc);
       const df lx = df_subz(df_addz(pxp, pxm), p2);
@@ -356,27 +365,59 @@ __device__ __forceinline__ void xfwd_rg_body(GridDev g, StencilIn in, DevScalars
       const df lap = df_addz(df_addz(df_mulz(lx, lcx), df_mulz(ly, lcy)), df_mulz(lz, lcz));
       return df_to_f(df_subz(df_subz(fv, fmean), lap));
     };
-    rgfft::run<T, false, M, 2, false>(
-        [&](int e) -> cpx<T> {
-          if (!valid) return {(T)0, (T)0};
-          const int i0 = 2 * e;
-          const float4 c = pc4[e];
-          const df pxm = pl[i0 == 0 ? nx - 1 : i0 - 1];
-          const df pxp = pl[i0 + 2 == nx ? 0 : i0 + 2];
-          const float4 zm = pzm4[e], zp = pzp4[e];
-          const float4 ym = has_ym ? pym4[e] : c;  // wall mirror below the bottom cell
-          // above the top cell: the wall mirror, or the outflow ghost -p (p = 0 on the face)
-          const float4 yp = has_yp ? pyp4[e] : (OPEN ? make_float4(-c.x, -c.y, -c.z, -c.w) : c);
-          const float4 fv = f4[e];
-          const df a0 = {c.x, c.y}, a1 = {c.z, c.w};
-          const float r0 = res(a0, pxm, a1, df{ym.x, ym.y}, df{yp.x, yp.y}, df{zm.x, zm.y}, df{zp.x, zp.y},
-                               df{fv.x, fv.y});
-          const float r1 = res(a1, a0, pxp, df{ym.z, ym.w}, df{yp.z, yp.w}, df{zm.z, zm.w}, df{zp.z, zp.w},
-                               df{fv.z, fv.w});
-          vmax = fmaxf(vmax, fmaxf(fabsf(r0), fabsf(r1)));
-          return {r0, r1};
-        },
-        put, buf + ll * LS, 1, t0, tws);
+    // the cells 2e, 2e+1 of the line with their neighbours, as pairs (P32: from
+    // the FP32 p, low parts zero)
+    auto cell2 = [&](int e, auto P32) -> cpx<T> {
+      constexpr bool F = decltype(P32)::value;
+      const int i0 = 2 * e;
+      float4 c, zm, zp, ym, yp;
+      df pxm, pxp;
+      if constexpr (F) {
+        const float2 c2 = qc2[e], zm2 = qzm2[e], zp2 = qzp2[e];
+        c = make_float4(c2.x, 0.0f, c2.y, 0.0f);
+        zm = make_float4(zm2.x, 0.0f, zm2.y, 0.0f);
+        zp = make_float4(zp2.x, 0.0f, zp2.y, 0.0f);
+        pxm = {ql[i0 == 0 ? nx - 1 : i0 - 1], 0.0f};
+        pxp = {ql[i0 + 2 == nx ? 0 : i0 + 2], 0.0f};
+        if (has_ym) {
+          const float2 v = qym2[e];
+          ym = make_float4(v.x, 0.0f, v.y, 0.0f);
+        } else {
+          ym = c;
+        }
+        if (has_yp) {
+          const float2 v = qyp2[e];
+          yp = make_float4(v.x, 0.0f, v.y, 0.0f);
+        } else {
+          yp = OPEN ? make_float4(-c.x, -c.y, -c.z, -c.w) : c;
+        }
+      } else {
+        c = pc4[e];
+        pxm = pl[i0 == 0 ? nx - 1 : i0 - 1];
+        pxp = pl[i0 + 2 == nx ? 0 : i0 + 2];
+        zm = pzm4[e];
+        zp = pzp4[e];
+        ym = has_ym ? pym4[e] : c;  // wall mirror below the bottom cell
+        // above the top cell: the wall mirror, or the outflow ghost -p (p = 0 on the face)
+        yp = has_yp ? pyp4[e] : (OPEN ? make_float4(-c.x, -c.y, -c.z, -c.w) : c);
+      }
+      const float4 fv = f4[e];
+      const df a0 = {c.x, c.y}, a1 = {c.z, c.w};
+      const float r0 = res(a0, pxm, a1, df{ym.x, ym.y}, df{yp.x, yp.y}, df{zm.x, zm.y}, df{zp.x, zp.y},
+                           df{fv.x, fv.y});
+      const float r1 = res(a1, a0, pxp, df{ym.z, ym.w}, df{yp.z, yp.w}, df{zm.z, zm.w}, df{zp.z, zp.w},
+                           df{fv.z, fv.w});
+      vmax = fmaxf(vmax, fmaxf(fabsf(r0), fabsf(r1)));
+      return {r0, r1};
+    };
+    if (p0f)
+      rgfft::run<T, false, M, 2, false>(
+          [&](int e) -> cpx<T> { return valid ? cell2(e, std::true_type{}) : cpx<T>{(T)0, (T)0}; }, put,
+          buf + ll * LS, 1, t0, tws);
+    else
+      rgfft::run<T, false, M, 2, false>(
+          [&](int e) -> cpx<T> { return valid ? cell2(e, std::false_type{}) : cpx<T>{(T)0, (T)0}; }, put,
+          buf + ll * LS, 1, t0, tws);
   }
   if (SRC == SRC_F) block_max_to(&sc->fmax_bits, vmax);
   else if (SRC == SRC_RESID) block_max_to(&sc->rmax_bits[slot], vmax);  // float max, widened once per warp
@@ -1001,7 +1042,8 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, const cpx<T>* __restric
 template <int MODE, int M, bool PL = false>
 __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, double* p, df* pdf,
                                                  double scale, const cpx<float>* tw, int L,
-                                                 const DevScalars* sc, DevScalars* psc, uint32_t bid, uint32_t nblk) {
+                                                 const DevScalars* sc, DevScalars* psc, uint32_t bid, uint32_t nblk,
+                                                 float* p32 = nullptr) {
   using T = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (sc && sc->done) return;
@@ -1063,6 +1105,11 @@ __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, 
     const uint32_t o = c0 + 2 * (uint32_t)n;
     if (MODE == XI_F64) {
       reinterpret_cast<double2*>(p)[o >> 1] = make_double2(scale * (double)v.x, scale * (double)v.y);
+    } else if (MODE == XI_F32) {
+      // the pair s x has a zero low part (s a power of two): its high part is p
+      const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
+      reinterpret_cast<float2*>(p32)[o >> 1] = make_float2(d0.hi, d1.hi);
+      psum = df_addz(df_addz(psum, d0), d1);
     } else {
       const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
       float4* q4 = reinterpret_cast<float4*>(pdf) + (o >> 1);
@@ -1085,6 +1132,9 @@ __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, 
                                   buf + ll * LS, 1, t0, tws);
     __syncthreads();
     const uint32_t l0 = bid * (uint32_t)L;
+    // the first sweep adds to the first solve's p in FP32 where it was kept so
+    // (a pair with a zero low part: the same sums)
+    const bool from32 = p32 != nullptr && psc != nullptr && psc->iter == 1;
     constexpr int U = 4;
     for (int b0 = threadIdx.x; b0 < L * M; b0 += U * blockDim.x) {
       float4 q[U];
@@ -1092,8 +1142,15 @@ __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, 
       for (int u = 0; u < U; ++u) {
         const int idx = b0 + u * blockDim.x;
         const int lq = idx / M;
-        if (idx < L * M && l0 + lq < nlines)
-          q[u] = reinterpret_cast<const float4*>(pdf)[(l0 + lq) * (uint32_t)M + (idx - lq * M)];
+        if (idx < L * M && l0 + lq < nlines) {
+          const uint32_t o2 = (l0 + lq) * (uint32_t)M + (idx - lq * M);
+          if (from32) {
+            const float2 a = reinterpret_cast<const float2*>(p32)[o2];
+            q[u] = make_float4(a.x, 0.0f, a.y, 0.0f);
+          } else {
+            q[u] = reinterpret_cast<const float4*>(pdf)[o2];
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -1117,9 +1174,9 @@ __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, 
 template <int MODE, int M, bool PL = false>
 __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __restrict__ spec, double* p, df* pdf,
                                                  double scale, const cpx<float>* __restrict__ tw, int L,
-                                                 const DevScalars* sc, DevScalars* psc) {
+                                                 const DevScalars* sc, DevScalars* psc, float* p32) {
   pdl_enter();
-  xinv_rg_body<MODE, M, PL>(g, spec, p, pdf, scale, tw, L, sc, psc, blockIdx.x, gridDim.x);
+  xinv_rg_body<MODE, M, PL>(g, spec, p, pdf, scale, tw, L, sc, psc, blockIdx.x, gridDim.x, p32);
 }
 
 // ---------------------------------------------------------------------------
@@ -1128,6 +1185,12 @@ __global__ void __launch_bounds__(256) k_xinv_rg(GridDev g, const cpx<float>* __
 // Lines per CTA of the register-staged passes: the tuned tile, raised so that a
 // CTA (L * N/16 threads) holds at least one full warp and capped so that it
 // holds at most 256 threads (the kernels' launch bound).
+// (nx/2) nz a power of two: the inverse transforms' scaling 1/((nx/2) nz) is exact in FP32
+inline bool is_pow2_scale(const GridDev& g) {
+  const unsigned m = (unsigned)(g.nx / 2) * (unsigned)g.nz;
+  return m != 0u && (m & (m - 1u)) == 0u;
+}
+
 template <int N>
 int rg_lines(int tile) {
   constexpr int lo = 32 / (N / 16) > 1 ? 32 / (N / 16) : 1, hi = 256 / (N / 16);
@@ -1321,7 +1384,7 @@ cudaError_t launch_ydct(const GridDev& g, cpx<T>* spec, const RadixPlan& rp, con
 template <typename T>
 cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* p, df* pdf, double scale,
                         const RadixPlan& rp, const cpx<T>* tw, int lpb, const DevScalars* sc, DevScalars* psc,
-                        cudaStream_t st) {
+                        cudaStream_t st, float* p32) {
   const int nlines = g.ny * g.nz;
   const int grid = (nlines + lpb - 1) / lpb;
   const size_t sm = xinv_smem<T>(g.nx, lpb);
@@ -1339,19 +1402,23 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
         cudaError_t e2 = allow_smem(kernel, smr);
         if (e2 != cudaSuccess) return e2;
         launch_pdl(kernel, gr, L * (N / 16), smr, st, g, (const cpx<float>*)spec, p, pdf, scale, (const cpx<float>*)tw, L,
-                                               sc, psc);
+                                               sc, psc, p32);
         return cudaGetLastError();
       };
+      if (mode == XI_F32 && !(p32 && is_pow2_scale(g))) return cudaErrorInvalidValue;
       if (g.spec_planes) {
         if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N, true>);
         if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N, true>);
+        if (mode == XI_F32) return go(k_xinv_rg<XI_F32, N, true>);
         return go(k_xinv_rg<XI_DF_ACC, N, true>);
       }
       if (mode == XI_F64) return go(k_xinv_rg<XI_F64, N>);
       if (mode == XI_DF) return go(k_xinv_rg<XI_DF, N>);
+      if (mode == XI_F32) return go(k_xinv_rg<XI_F32, N>);
       return go(k_xinv_rg<XI_DF_ACC, N>);
       }
     }
+    if (mode == XI_F32 || p32) return cudaErrorInvalidValue;  // FP32 p: the register-staged passes only
     if (g.spec_planes) return cudaErrorInvalidValue;  // plane layout: power-of-two nx/2 only
     if (mode == XI_F64) {
       if ((e = allow_smem(k_xinv<T, XI_F64, N>, sm)) != cudaSuccess) return e;
@@ -1384,7 +1451,7 @@ cudaError_t launch_xinv(int mode, const GridDev& g, const cpx<T>* spec, double* 
                                       const T*, const T*, const T*, int, const DevScalars*, cudaStream_t);       \
   template cudaError_t launch_xinv<T>(int, const GridDev&, const cpx<T>*, double*, df*, double,                  \
                                       const RadixPlan&, const cpx<T>*, int, const DevScalars*, DevScalars*,      \
-                                      cudaStream_t);
+                                      cudaStream_t, float*);
 
 
 }  // namespace ppe
