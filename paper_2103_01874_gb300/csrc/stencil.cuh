@@ -58,6 +58,11 @@ __device__ __forceinline__ df beta_df(df a, df b, const StencilConst& K, int rul
 // ch gh = 1, u_pre = gh Q~: one product of the flux instead of a product and
 // a sum (the two differ by the pair rounding of the constants, ~1e-14
 // relative, and D u_pre = (dt/rho_0)(f + (rho_0/dt) S) holds either way).
+// Both are left unnormalised (see the lazy operations in dfloat.cuh): every
+// consumer -- the divergence, the correction's subtraction and its exact
+// conversion to FP64 -- takes them through lazy pair operations, and a
+// normalisation only rewrites the same value (about 5 % fewer instructions
+// in the right-hand-side kernels).
 struct FaceOut {
   df q, upre;
 };
@@ -65,8 +70,8 @@ __device__ __forceinline__ FaceOut face_q(df rl, df rh, df pl, df ph, df us, df 
                                           int rule) {
   const df bg = df_mulz(beta_df(rl, rh, K, rule), df_subz(ph, pl));
   FaceOut o;
-  o.q = df_norm(df_addz(bg, df_mulz(ch, us)));
-  o.upre = df_norm(df_mulz(gh, o.q));
+  o.q = df_addz(bg, df_mulz(ch, us));
+  o.upre = df_mulz(gh, o.q);
   return o;
 }
 
