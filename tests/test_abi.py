@@ -72,3 +72,35 @@ def test_null_arguments_rejected(lib):
     assert lib.ppe_plan(ctypes.byref(h), ctypes.byref(g), None, None) == 2
     g = ppe.Grid(8, 8, 8, -1.0, 1.0, 1.0)
     assert lib.ppe_plan(ctypes.byref(h), ctypes.byref(g), None, None) == 1
+
+
+def test_workspace_counts_the_fp32_first_solve_pressure(lib):
+    """ppe_project keeps the first solve's p in FP32 (4 B per cell more
+    workspace) exactly where the inverse transforms' scaling 1/((nx/2) nz) is a
+    power of two and nx/2 has a register-staged length (16 .. 256), in the FP32
+    form with at least one sweep; the bench's byte accounting makes the same
+    call."""
+    import ctypes
+    import bench
+
+    def ws(shape, precision, sweeps):
+        g = ppe.Grid(*shape, 1.0, 1.0, 1.0)
+        o = ppe.Options(precision, 0, 1e-10, sweeps, 1e-12)
+        return lib.ppe_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
+
+    cases = [((256, 256, 256), True), ((64, 48, 32), True), ((512, 64, 64), True), ((32, 8, 16), True),
+             ((1024, 8, 8), False),   # nx/2 = 512: no compiled register-staged length
+             ((384, 256, 384), False),  # nx/2 = 192 not a power of two
+             ((256, 64, 48), False),  # (nx/2) nz = 6144 not a power of two
+             ((24, 16, 16), False)]   # nx/2 = 12 below 16
+    for shape, eligible in cases:
+        n = shape[0] * shape[1] * shape[2]
+        extra = ws(shape, ppe.FP32_REFINE, 4) - ws(shape, ppe.FP32_REFINE, 0)
+        assert extra == (4 * n if eligible else 0), (shape, extra)
+        assert ws(shape, ppe.FP64, 4) == ws(shape, ppe.FP64, 0)
+        old = (bench.NX, bench.NY, bench.NZ)
+        try:
+            bench.NX, bench.NY, bench.NZ = shape
+            assert bench.p0_fp32() == eligible, shape
+        finally:
+            bench.NX, bench.NY, bench.NZ = old
