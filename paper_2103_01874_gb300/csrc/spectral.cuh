@@ -1135,35 +1135,47 @@ __device__ __forceinline__ void xinv_rg_body(GridDev g, const cpx<float>* spec, 
     // the first sweep adds to the first solve's p in FP32 where it was kept so
     // (a pair with a zero low part: the same sums)
     const bool from32 = p32 != nullptr && psc != nullptr && psc->iter == 1;
-    constexpr int U = 4;
-    for (int b0 = threadIdx.x; b0 < L * M; b0 += U * blockDim.x) {
-      float4 q[U];
+    // U cell pairs in flight per thread: their old p (four floats as pairs, two
+    // as FP32 -- twice as many loads for the same registers), then the updates
+    auto update = [&](auto UC, auto F32) {
+      constexpr int U = decltype(UC)::value;
+      constexpr bool FROM32 = decltype(F32)::value;
+      using Old = typename std::conditional<FROM32, float2, float4>::type;
+      for (int b0 = threadIdx.x; b0 < L * M; b0 += U * blockDim.x) {
+        Old q[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = b0 + u * blockDim.x;
-        const int lq = idx / M;
-        if (idx < L * M && l0 + lq < nlines) {
-          const uint32_t o2 = (l0 + lq) * (uint32_t)M + (idx - lq * M);
-          if (from32) {
-            const float2 a = reinterpret_cast<const float2*>(p32)[o2];
-            q[u] = make_float4(a.x, 0.0f, a.y, 0.0f);
+        for (int u = 0; u < U; ++u) {
+          const int idx = b0 + u * blockDim.x;
+          const int lq = idx / M;
+          if (idx < L * M && l0 + lq < nlines)
+            q[u] = reinterpret_cast<const Old*>(FROM32 ? (const void*)p32 : (const void*)pdf)
+                [(l0 + lq) * (uint32_t)M + (idx - lq * M)];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = b0 + u * blockDim.x;
+          const int lq = idx / M, n = idx - lq * M;
+          if (idx >= L * M || l0 + lq >= nlines) continue;
+          const cpx<T> v = buf[lq * LS + rgfft::row(n)];
+          const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
+          df a0, a1;
+          if constexpr (FROM32) {
+            a0 = {q[u].x, 0.0f};
+            a1 = {q[u].y, 0.0f};
           } else {
-            q[u] = reinterpret_cast<const float4*>(pdf)[o2];
+            a0 = {q[u].x, q[u].y};
+            a1 = {q[u].z, q[u].w};
           }
+          const df s0 = df_add(a0, d0), s1 = df_add(a1, d1);
+          reinterpret_cast<float4*>(pdf)[(l0 + lq) * (uint32_t)M + n] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+          psum = df_addz(df_addz(psum, s0), s1);
         }
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = b0 + u * blockDim.x;
-        const int lq = idx / M, n = idx - lq * M;
-        if (idx >= L * M || l0 + lq >= nlines) continue;
-        const cpx<T> v = buf[lq * LS + rgfft::row(n)];
-        const df d0 = df_mul_f(sdf, (float)v.x), d1 = df_mul_f(sdf, (float)v.y);
-        const df s0 = df_add(df{q[u].x, q[u].y}, d0), s1 = df_add(df{q[u].z, q[u].w}, d1);
-        reinterpret_cast<float4*>(pdf)[(l0 + lq) * (uint32_t)M + n] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
-        psum = df_addz(df_addz(psum, s0), s1);
-      }
-    }
+    };
+    if (from32)
+      update(std::integral_constant<int, 8>{}, std::true_type{});
+    else
+      update(std::integral_constant<int, 4>{}, std::false_type{});
   }
   if (MODE != XI_F64 && psc) {
     // per-CTA sum of p, totalled in a fixed order by the next z pass (finish_sums)
